@@ -1,0 +1,206 @@
+"""ctypes binding of the FP64 oracle in oracle.c (test infrastructure only).
+
+Inputs are the caller's arrays promoted exactly to float64 (float32 values are
+exactly representable), so the oracle evaluates the same system the CUDA
+library is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_d = ctypes.POINTER(ctypes.c_double)
+_i = ctypes.POINTER(ctypes.c_int)
+_l = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (-O2, OpenMP, no fast-math) into liboracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
+                               "-D_GNU_SOURCE", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        common = [ctypes.c_int, _d, _d, _i, ctypes.c_int, _d, _d]
+        _lib.or_brute.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, _d, _d, _d, _l]
+        _lib.or_celllist.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int, _i, _d, _d, _d, _l]
+        _lib.or_listset.argtypes = common + [_d, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_int64, _l,
+                                             _d, _d, _d, _l]
+        _lib.or_pairs_within.argtypes = [ctypes.c_int, _d, _d, _i, _i, ctypes.c_double,
+                                         ctypes.c_int64, _l]
+        _lib.or_pairs_within.restype = ctypes.c_int64
+        _lib.or_vjp.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, _d, ctypes.c_double, _d,
+                                         _d, _d, _d]
+        _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_set_num_threads.argtypes = [ctypes.c_int]
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _arrays(sys_or_kw):
+    s = sys_or_kw
+    x = np.ascontiguousarray(s.x, dtype=np.float64)
+    q = np.ascontiguousarray(s.q, dtype=np.float64)
+    ty = np.ascontiguousarray(s.types, dtype=np.int32)
+    c6 = np.ascontiguousarray(s.c6, dtype=np.float64)
+    c12 = np.ascontiguousarray(s.c12, dtype=np.float64)
+    off = np.ascontiguousarray(s.excl_off, dtype=np.int32)
+    idx = np.ascontiguousarray(s.excl_idx, dtype=np.int32)
+    if idx.size == 0:
+        idx = np.zeros(1, dtype=np.int32)
+    box = np.ascontiguousarray(s.box, dtype=np.float64)
+    return x, q, ty, c6, c12, off, idx, box
+
+
+def _coul(s):
+    eps_rf = s.eps_rf if math.isfinite(s.eps_rf) else math.inf
+    return int(s.coulomb), float(s.eps_r), float(eps_rf), float(s.beta)
+
+
+def brute(s, x=None):
+    """O(N^2) evaluation. Returns dict(F [N,3], E_lj, E_c, W [3,3], npairs)."""
+    lib = _load()
+    xx, q, ty, c6, c12, off, idx, box = _arrays(s)
+    if x is not None:
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+    n = xx.shape[0]
+    F = np.zeros((n, 3))
+    E = np.zeros(2)
+    W = np.zeros(9)
+    npairs = ctypes.c_int64(0)
+    co, er, erf_, be = _coul(s)
+    rc = lib.or_brute(n, _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d), _p(c12, _d),
+                      _p(off, _i), _p(idx, _i), _p(box, _d), co, er, erf_, be, float(s.rc),
+                      _p(F, _d), _p(E, _d), _p(W, _d), ctypes.byref(npairs))
+    if rc != 0:
+        raise ValueError("oracle: rc must be < L/2")
+    return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=npairs.value)
+
+
+def celllist(s, x=None, subset=None):
+    """Cell-list evaluation (all cores).  With subset: forces on those atoms only."""
+    lib = _load()
+    xx, q, ty, c6, c12, off, idx, box = _arrays(s)
+    if x is not None:
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+    n = xx.shape[0]
+    co, er, erf_, be = _coul(s)
+    if subset is not None:
+        sub = np.ascontiguousarray(subset, dtype=np.int32)
+        F = np.zeros((sub.size, 3))
+        E = np.zeros(2)
+        W = np.zeros(9)
+        rc = lib.or_celllist(n, _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d),
+                             _p(c12, _d), _p(off, _i), _p(idx, _i), _p(box, _d), co, er, erf_, be,
+                             float(s.rc), sub.size, _p(sub, _i), _p(F, _d), _p(E, _d), _p(W, _d),
+                             None)
+        if rc != 0:
+            raise ValueError("oracle: subset evaluation needs >= 3 cells per axis and rc < L/2")
+        return dict(F=F)
+    F = np.zeros((n, 3))
+    E = np.zeros(2)
+    W = np.zeros(9)
+    npairs = ctypes.c_int64(0)
+    rc = lib.or_celllist(n, _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d), _p(c12, _d),
+                         _p(off, _i), _p(idx, _i), _p(box, _d), co, er, erf_, be, float(s.rc), 0,
+                         None, _p(F, _d), _p(E, _d), _p(W, _d), ctypes.byref(npairs))
+    if rc != 0:
+        raise ValueError("oracle: rc must be < L/2")
+    return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=npairs.value)
+
+
+def listset(s, pairs, x=None):
+    """Sum exactly the given image pairs [(i, j, sx, sy, sz)] that lie inside rc."""
+    lib = _load()
+    xx, q, ty, c6, c12, off, idx, box = _arrays(s)
+    if x is not None:
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+    pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 5)
+    if pr.shape[0] == 0:
+        pr = np.zeros((1, 5), dtype=np.int64)
+        npair = 0
+    else:
+        npair = pr.shape[0]
+    n = xx.shape[0]
+    F = np.zeros((n, 3))
+    E = np.zeros(2)
+    W = np.zeros(9)
+    n_in = ctypes.c_int64(0)
+    co, er, erf_, be = _coul(s)
+    rc = lib.or_listset(n, _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d), _p(c12, _d),
+                        _p(box, _d), co, er, erf_, be, float(s.rc), npair, _p(pr, _l), _p(F, _d),
+                        _p(E, _d), _p(W, _d), ctypes.byref(n_in))
+    if rc != 0:
+        raise ValueError("oracle: pair index out of range")
+    return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=n_in.value)
+
+
+def pairs_within(s, rcut, x=None):
+    """Brute-force set of unordered non-excluded pairs within rcut: int64 [P,5]."""
+    lib = _load()
+    xx, q, ty, c6, c12, off, idx, box = _arrays(s)
+    if x is not None:
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+    n = xx.shape[0]
+    cap = 1 << 16
+    while True:
+        out = np.zeros((cap, 5), dtype=np.int64)
+        cnt = lib.or_pairs_within(n, _p(xx, _d), _p(box, _d), _p(off, _i), _p(idx, _i),
+                                  float(rcut), cap, _p(out, _l))
+        if cnt <= cap:
+            return out[:cnt]
+        cap = int(cnt)
+
+
+def vjp(s, gF, gE, x=None):
+    """Analytic gradients of <gF, F> + gE*E: dict(gx [N,3], gq [N], gc6 [T,T], gc12 [T,T])."""
+    lib = _load()
+    xx, q, ty, c6, c12, off, idx, box = _arrays(s)
+    if x is not None:
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+    n = xx.shape[0]
+    T = c6.shape[0]
+    g = np.ascontiguousarray(gF, dtype=np.float64)
+    gx = np.zeros((n, 3))
+    gq = np.zeros(n)
+    gc6 = np.zeros((T, T))
+    gc12 = np.zeros((T, T))
+    co, er, erf_, be = _coul(s)
+    rc = lib.or_vjp(n, _p(xx, _d), _p(q, _d), _p(ty, _i), T, _p(c6, _d), _p(c12, _d), _p(off, _i),
+                    _p(idx, _i), _p(box, _d), co, er, erf_, be, float(s.rc), _p(g, _d), float(gE),
+                    _p(gx, _d), _p(gq, _d), _p(gc6, _d), _p(gc12, _d))
+    if rc != 0:
+        raise ValueError("oracle: rc must be < L/2")
+    return dict(gx=gx, gq=gq, gc6=gc6, gc12=gc12)
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+def set_num_threads(t: int) -> None:
+    _load().or_set_num_threads(int(t))
