@@ -1,0 +1,489 @@
+"""Benchmark of the short-range non-bonded path (one JSON line on stdout).
+
+Default workload: the 96,000-atom SPC/E water box (Ewald real space, rc 1.0 nm,
+rlist 1.1 nm) run as an MD-like loop: every step evaluates forces, energies
+and the virial from the inner list, re-prunes half of the outer list (rolling
+prune over 2 parts) and advances positions ballistically; every 100 steps the
+grid sort and the pair search rebuild the outer list.  `value` is steps (force
+evaluations) per second on the device; `e2e` the same through the public API
+with positions copied in from pinned host memory and forces/energies copied out
+every step.  Extra workloads (batched replicas, forward + adjoint, the 1.5M-atom
+box) are reported under "extra".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--full]
+
+--impl reference times the FP64 CPU oracle (the reference arm) on the same
+workload and metric.  Under torchrun each rank evaluates its own independent
+copy of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "force-evals/s plain vs batched vs fwd+adjoint; %FP32 peak; RMS rel err≤1e-5"
+UNIT = "force-evals/s"
+NSTLIST = 100
+N_PARTS = 2
+DT = 0.002  # ps
+
+# FP32 operations per effective pair interaction (inside rc) by flavour, counted
+# from the pair formulas ("Roofline"): distance 8, 1/r and powers 4,
+# LJ force 5, Coulomb force (Ewald rational 29 / reaction field 5), scalar sum 1,
+# force vector 3 and the i/j accumulation 6; energies add LJ 4, Coulomb (Ewald
+# exp*rational 16 / RF 8), accumulation 2; the virial adds 2 per pair (amortised).
+FLOPS_PER_PAIR = {
+    ("ewald", "F"): 56, ("ewald", "FE"): 78, ("ewald", "FEV"): 80,
+    ("rf", "F"): 32, ("rf", "FE"): 46, ("rf", "FEV"): 48,
+}
+
+
+def rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fp32_peak_tflops(sm_mhz):
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz if sm_mhz else 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms
+
+
+def l2_flusher(device):
+    import torch
+    buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    def flush():
+        buf.fill_(1.0)
+    return flush
+
+
+# ----------------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2006_09167_gb300 import api, synth
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    s = synth.water_96k(seed=2 + 1000 * rank)
+    ctx = api.NbContext.from_system(s)
+    x0 = torch.tensor(s.x, device=dev)
+    v = torch.tensor(synth.maxwell_boltzmann(s, 300.0, seed=7 + rank), dtype=torch.float32, device=dev)
+    flush = l2_flusher(dev)
+    box = s.box
+    ctx.build(x0, box)
+    ctx.nb_trace_enable(True)
+    f = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
+    e = torch.empty(2, dtype=torch.float64, device=dev)
+    w = torch.empty(9, dtype=torch.float64, device=dev)
+    flags = api.NB_ENERGY | api.NB_VIRIAL
+    x = x0.clone()
+
+    def step(t):
+        if t % NSTLIST == 0 and t > 0:
+            ctx.build(x, box)
+        ctx.nb_forces(flags, x, f, e, w)
+        ctx.nb_prune_rolling(t % N_PARTS, N_PARTS)
+        x.add_(v, alpha=DT)
+
+    for t in range(args.warmup):
+        step(t)
+    torch.cuda.synchronize()
+    for kind in range(4):
+        ctx.nb_trace_read(kind)
+    launches0 = ctx.nb_get_stats()["n_launches"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for k in range(args.steps):
+        flush()  # L2 flushed between timed steps (outside the events)
+        evs[k][0].record()
+        step(args.warmup + k)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    launches = ctx.nb_get_stats()["n_launches"] - launches0
+    fk_ms, fk_n = ctx.nb_trace_read(api.NB_TRACE_FORCES)
+    pr_ms, pr_n = ctx.nb_trace_read(api.NB_TRACE_PRUNE)
+    ga_ms, ga_n = ctx.nb_trace_read(api.NB_TRACE_GATHER)
+    ctx.nb_trace_enable(False)
+    assert ctx.nb_get_error() == 0, "device error during the timed loop"
+    # algorithmic work of one force launch: effective pairs at the current positions
+    n_eff, n_raw = ctx.nb_count_pairs()
+    res = dict(total_ms=total_ms, step_ms=step_ms, launches=launches, fk_ms=fk_ms, fk_n=fk_n, pr_ms=pr_ms,
+               pr_n=pr_n, ga_ms=ga_ms, ga_n=ga_n, n_eff=n_eff, n_raw=n_raw, clocks=clk, n_atoms=s.n)
+    # end to end through the public API: pinned host positions in, forces + energies out
+    xh = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
+    xh.copy_(x.cpu())
+    fh = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
+    eh = torch.empty(2, dtype=torch.float64).pin_memory()
+    wh = torch.empty(9, dtype=torch.float64).pin_memory()
+    xd = torch.empty_like(x)
+    vh = v.cpu()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = 2 * NSTLIST + k
+        xd.copy_(xh, non_blocking=True)
+        if t % NSTLIST == 0:
+            ctx.build(xd, box)
+        fo, eo, wo = ctx.forces(xd, energy=True, virial=True)
+        ctx.nb_prune_rolling(t % N_PARTS, N_PARTS)
+        fh.copy_(fo, non_blocking=True)
+        eh.copy_(eo, non_blocking=True)
+        wh.copy_(wo.view(-1), non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        xh.add_(vh, alpha=DT)
+    res["e2e_ms"] = float(np.mean(e2e_ms))
+    res["h2d"] = s.n * 3 * 4
+    res["d2h"] = s.n * 3 * 4 + 16 + 72
+    return res
+
+
+def extra_workloads(args):
+    """Batched replicas (plain vs batched vs per-replica graph) and forward + adjoint."""
+    import torch
+    from paper_2006_09167_gb300 import api, synth
+    out = {}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # batched: 256 uneven replicas
+    reps = synth.replica_set()
+    ctxs, xs = [], []
+    for sysr in reps:
+        c = api.NbContext.from_system(sysr)
+        xr = torch.tensor(sysr.x, device=dev)
+        c.build(xr, sysr.box)
+        ctxs.append(c)
+        xs.append(xr)
+    b = api.NbBatch(ctxs)
+    xcat = torch.cat(xs).contiguous()
+    fcat = torch.empty_like(xcat)
+    R = len(ctxs)
+    e = torch.empty(2 * R, dtype=torch.float64, device=dev)
+    w = torch.empty(9 * R, dtype=torch.float64, device=dev)
+    flags = api.NB_ENERGY | api.NB_VIRIAL
+    fs = [torch.empty_like(xr) for xr in xs]
+    es = [torch.empty(2, dtype=torch.float64, device=dev) for _ in xs]
+    ws = [torch.empty(9, dtype=torch.float64, device=dev) for _ in xs]
+    flush = l2_flusher(dev)
+
+    def batched():
+        b.nb_forces_batched(flags, xcat, fcat, e, w)
+
+    def plain():
+        for c, xr, fr, er, wr in zip(ctxs, xs, fs, es, ws):
+            c.nb_forces(flags, xr, fr, er, wr)
+
+    def time_fn(fn, reps_=20, warm=3):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps_):
+            flush()
+            a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            bb.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(bb))
+        return float(np.median(ts))
+
+    def graphed(fn):
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            fn()
+        torch.cuda.current_stream().wait_stream(st)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    gb = graphed(batched)
+    gp = graphed(plain)
+    t_batched_graph = time_fn(gb.replay)
+    t_plain_graph = time_fn(gp.replay)
+    t_plain_seq = time_fn(plain, reps_=5, warm=1)
+    n_all = sum(c.n for c in ctxs)
+    out["batched_256_replicas"] = {
+        "atoms_total": int(n_all), "replicas": R,
+        "batched_graph_ms": t_batched_graph, "plain_graph_ms": t_plain_graph, "plain_sequential_ms": t_plain_seq,
+        "system_evals_per_s_batched": R * 1e3 / t_batched_graph,
+        "system_evals_per_s_plain_graph": R * 1e3 / t_plain_graph,
+        "system_evals_per_s_plain_sequential": R * 1e3 / t_plain_seq,
+    }
+    del gb, gp, b, ctxs, xs
+    # forward + adjoint on the 24k box with 6 LJ types
+    s4 = synth.water_24k_types()
+    c4 = api.NbContext.from_system(s4)
+    x4 = torch.tensor(s4.x, device=dev)
+    c4.build(x4, s4.box)
+    T = s4.n_types
+    gF = torch.randn((s4.n, 3), device=dev)
+    gx = torch.empty_like(x4)
+    gq = torch.empty(s4.n, device=dev)
+    g6 = torch.empty((T, T), dtype=torch.float64, device=dev)
+    g12 = torch.empty_like(g6)
+    f4 = torch.empty_like(x4)
+    e4 = torch.empty(2, dtype=torch.float64, device=dev)
+
+    def fwd():
+        c4.nb_forces(api.NB_ENERGY, x4, f4, e4)
+
+    def fwd_adj():
+        c4.nb_forces(api.NB_ENERGY, x4, f4, e4)
+        c4.nb_forces_vjp(x4, gF, 0.5, gx, gq, g6, g12)
+
+    t_f = time_fn(graphed(fwd).replay)
+    t_fa = time_fn(graphed(fwd_adj).replay)
+    out["fwd_adjoint_24k"] = {"n_atoms": s4.n, "forward_ms": t_f, "forward_adjoint_ms": t_fa,
+                              "evals_per_s_forward": 1e3 / t_f, "evals_per_s_forward_adjoint": 1e3 / t_fa}
+    if args.full:
+        s3 = synth.polymer_water_box()
+        c3 = api.NbContext.from_system(s3)
+        x3 = torch.tensor(s3.x, device=dev)
+        c3.build(x3, s3.box)
+        f3 = torch.empty_like(x3)
+        e3 = torch.empty(2, dtype=torch.float64, device=dev)
+        w3 = torch.empty(9, dtype=torch.float64, device=dev)
+        t3 = time_fn(lambda: c3.nb_forces(flags, x3, f3, e3, w3), reps_=10)
+        n_eff, n_raw = c3.nb_count_pairs()
+        out["polymer_water_1.5M"] = {"n_atoms": s3.n, "force_ms": t3, "evals_per_s": 1e3 / t3,
+                                     "effective_pairs": int(n_eff), "evaluated_pairs": int(n_raw)}
+    return out
+
+
+def cpu_oracle_sample(seconds=12.0):
+    """The FP64 cell-list oracle on the host cores: full 96k-atom evaluations."""
+    import oracle
+    from paper_2006_09167_gb300 import synth
+    s = synth.water_96k()
+    oracle.celllist(s)  # warm-up (page in, thread start)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds or n == 0:
+        oracle.celllist(s)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} full FP64 cell-list evaluations (forces, energies, virial) of the 96,000-atom box "
+                      f"in {dt:.1f} s"}
+
+
+def main_ours(args):
+    import torch
+    rank, world, local_rank = rank_env()
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    res = run_ours(args, rank, world, local_rank)
+    ms = res["total_ms"]
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        te = torch.tensor([res["e2e_ms"]], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        res["e2e_ms"] = float(te.item())
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    clk = res["clocks"]
+    peak, sms = fp32_peak_tflops(clk.get("sm_mhz"))
+    fk_avg_ms = res["fk_ms"] / max(res["fk_n"], 1)
+    alg_flops = res["n_eff"] * FLOPS_PER_PAIR[("ewald", "FEV")]
+    achieved = alg_flops / (fk_avg_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "spce_water_96k_ewald_rc1.0_rlist1.1 MD-like step: forces+energies+virial, "
+                               "rolling prune 1/2 per step, grid sort + pair search every 100 steps",
+                   "n_atoms": res["n_atoms"], "rc": 1.0, "rlist": 1.1, "nstlist": NSTLIST, "prune_parts": N_PARTS,
+                   "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                   "parallelism": f"replicas{world}"},
+        "e2e": {"value": world * 1e3 / res["e2e_ms"], "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
+                "d2h_bytes_per_step": res["d2h"]},
+        "gpu_launches": int(res["launches"]),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_forces<Ewald, energy, virial>", "avg_launch_ms": fk_avg_ms,
+                     "effective_pairs_per_launch": int(res["n_eff"]), "evaluated_pairs_per_launch": int(res["n_raw"]),
+                     "flops_per_effective_pair": FLOPS_PER_PAIR[("ewald", "FEV")],
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock under load"},
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons")},
+        "kernels_ms_per_step": {"forces": fk_avg_ms, "prune": res["pr_ms"] / max(res["pr_n"], 1),
+                                "gather": res["ga_ms"] / max(res["ga_n"], 1)},
+        "pairs_per_s_effective": res["n_eff"] / (fk_avg_ms * 1e-3),
+    }
+    if not args.no_extra:
+        try:
+            line["extra"] = extra_workloads(args)
+        except Exception as exc:  # report, do not hide the main number
+            line["extra"] = {"error": repr(exc)}
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------------ reference
+def main_reference(args):
+    """The FP64 oracle as the reference arm: same workload, metric and step definition."""
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2006_09167_gb300 import synth
+    s = synth.water_96k()
+    v = synth.maxwell_boltzmann(s, 300.0, seed=7)
+    x = s.x.astype(np.float64)
+    for t in range(args.warmup):
+        oracle.celllist(s, x=x)
+        x = x + DT * v
+    t0 = time.perf_counter()
+    for t in range(args.steps):
+        oracle.celllist(s, x=x)
+        x = x + DT * v
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "spce_water_96k_ewald_rc1.0_rlist1.1 MD-like step: exact FP64 cell-list "
+                                   "forces+energies+virial of every step (no pair list to prune)",
+                       "n_atoms": s.n, "rc": 1.0, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} timed full evaluations of the 96,000-atom box"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main_profile(args):
+    """A short, fixed launch sequence for profilers: one build, then force evaluations."""
+    import torch
+    from paper_2006_09167_gb300 import api, synth
+    s = synth.water_96k()
+    ctx = api.NbContext.from_system(s)
+    x = torch.tensor(s.x, device="cuda")
+    ctx.build(x, s.box)
+    f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+    e = torch.empty(2, dtype=torch.float64, device="cuda")
+    w = torch.empty(9, dtype=torch.float64, device="cuda")
+    for t in range(args.warmup + args.steps):
+        ctx.nb_forces(api.NB_ENERGY | api.NB_VIRIAL, x, f, e, w)
+        ctx.nb_prune_rolling(t % N_PARTS, N_PARTS)
+    torch.cuda.synchronize()
+    assert ctx.nb_get_error() == 0
+    print(json.dumps({"profile_case": "spce_water_96k_ewald", "launches": ctx.nb_get_stats()["n_launches"]}))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--full", action="store_true", help="also time the 1.5M-atom polymer/water box")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling target: warmup + steps force evaluations (energy+virial) of the 96k box only")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.profile:
+        main_profile(args)
+    elif args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * nb.h -- C ABI of the GB300 short-range non-bonded library.
+ *
+ * The library evaluates short-range non-bonded forces, energies and the virial
+ * for a periodic molecular system with the cluster pair algorithm of Pall et
+ * al., "Heterogeneous parallelization and acceleration of molecular dynamics
+ * simulations in GROMACS" (J. Chem. Phys. 153, 134110 (2020), arXiv:2006.09167):
+ *   - atoms are sorted on a grid that is regular in x,y and binned in z into
+ *     cells holding a fixed number of atoms; these cells are the 8-atom
+ *     clusters, grouped 2x2x2 into super-clusters (Sec. V.A, Fig. 4);
+ *   - a bounding-box search builds, per super-cluster, a joint list of
+ *     j-clusters with an 8-bit interaction mask telling which of the eight
+ *     i-clusters each j-cluster interacts with, plus exclusion bit masks
+ *     (Sec. V.A, Sec. V.D);
+ *   - an outer list built at a buffered cut-off rlist is pruned by atom-pair
+ *     distances into an inner list, in a rolling fashion (Sec. V.D, V.E);
+ *   - the pair kernel computes Lennard-Jones plus reaction-field or Ewald
+ *     real-space Coulomb interactions over the inner list, each pair once
+ *     (Newton's third law), masking excluded pairs and pairs beyond rc (Sec. V.A).
+ *
+ * Interaction forms (the paper names the interactions but gives no formulas):
+ *   V_LJ = C12/r^12 - C6/r^6 - (C12/rc^12 - C6/rc^6)
+ *   V_RF = f qi qj (1/r + k_rf r^2 - c_rf), k_rf = (eps_rf-eps_r)/((2 eps_rf+eps_r) rc^3),
+ *          c_rf = 1/rc + k_rf rc^2 (eps_rf = +inf: k_rf = 1/(2 rc^3))
+ *   V_Ew = f qi qj (erfc(beta r)/r - erfc(beta rc)/rc)
+ *   f = 138.935458/eps_r kJ mol^-1 nm e^-2; excluded pairs contribute nothing.
+ *   Virial W = -1/2 sum_pairs r_ij (x) F_ij.
+ * Units: nm, kJ/mol, e.  Boxes are rectangular; rc < L/2 and rlist < L per axis.
+ *
+ * Conventions for every call below:
+ *   - Pointers named *_dev are device pointers owned by the caller (contiguous,
+ *     on the current device).  Pointers named *_host are host pointers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued asynchronously on it unless the entry says it synchronises.
+ *   - Argument errors found on the host are returned directly and nothing is
+ *     enqueued.  Errors found on the device (non-finite coordinates, capacity
+ *     overflow) are recorded in a per-context flag read by nb_get_error().
+ *   - The context allocates device memory only in nb_create, nb_grid_sort and
+ *     nb_pairlist_build.  nb_prune_rolling, nb_forces, nb_forces_vjp and
+ *     nb_forces_batched never allocate.
+ *   - A context is not thread-safe; calls on one context must be ordered.
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx;
+typedef struct nb_batch nb_batch;
+
+typedef enum {
+    NB_OK = 0,
+    NB_ERR_INVALID_ARG = 1,   /* bad pointer, size, flag or parameter */
+    NB_ERR_BOX_TOO_SMALL = 2, /* rc >= L/2 or rlist >= L on some axis */
+    NB_ERR_NOT_READY = 3,     /* call out of order (e.g. forces before a pair list) */
+    NB_ERR_CAPACITY = 4,      /* an internal capacity was exceeded (see nb_get_error) */
+    NB_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    NB_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    NB_ERR_NONFINITE = 7      /* non-finite coordinates were seen on the device */
+} nb_status;
+
+enum { NB_COULOMB_RF = 0, NB_COULOMB_EWALD = 1 };
+
+/* flags of nb_forces / nb_forces_batched */
+enum { NB_ENERGY = 1u, NB_VIRIAL = 2u };
+
+/* which list nb_debug_export_pairs exports */
+enum { NB_LIST_OUTER = 0, NB_LIST_INNER = 1 };
+
+typedef struct {
+    int32_t n_atoms;  /* N >= 1 */
+    int32_t n_types;  /* T in [1, 64] */
+    int32_t coulomb;  /* NB_COULOMB_RF or NB_COULOMB_EWALD */
+    int32_t reserved; /* must be 0 */
+    double eps_r;     /* relative permittivity (> 0) */
+    double eps_rf;    /* reaction-field dielectric; +inf (or <= 0) = conducting */
+    double beta;      /* Ewald splitting parameter (nm^-1), 0 < beta*rc <= 4 */
+    double rc;        /* interaction cut-off (nm) */
+    double rlist;     /* outer pair-list cut-off, rlist >= r_in >= rc */
+    double r_in;      /* inner (pruned) list cut-off used by nb_pairlist_build */
+    const float *c6_host;  /* [T*T] row-major, symmetric, C6 (kJ mol^-1 nm^6) */
+    const float *c12_host; /* [T*T] row-major, symmetric, C12 (kJ mol^-1 nm^12) */
+} nb_params;
+
+/* Statistics of the current lists (nb_get_stats). */
+typedef struct {
+    int64_t n_atoms, n_slots, n_clusters, n_superclusters;
+    int64_t n_items;        /* work items (super-cluster, shift, j-range chunk) */
+    int64_t n_outer_j;      /* j-cluster entries in the outer list */
+    int64_t n_outer_bits;   /* set interaction-mask bits in the outer list */
+    int64_t n_mask_groups;  /* j-entries carrying explicit exclusion masks */
+    int64_t grid_nx, grid_ny;
+    int64_t n_launches;     /* kernels this context has launched so far */
+} nb_stats;
+
+/* kernels timed by the tracer (nb_trace_read) */
+enum { NB_TRACE_FORCES = 0, NB_TRACE_PRUNE = 1, NB_TRACE_GATHER = 2, NB_TRACE_VJP = 3, NB_TRACE_KINDS = 4 };
+
+/* Create a context for one system (Sec. V.A: positions, box, types, charges,
+ * exclusions and cut-offs define the problem).  q_host [N] charges, type_host
+ * [N] in [0,T), excl_off_host [N+1] / excl_idx_host [excl_off[N]]: symmetric
+ * exclusion lists in CSR form (an atom's own index is implicit and must not be
+ * listed; at most 16 partners per atom).  All inputs are copied; the caller
+ * keeps ownership.  Allocates device memory.  Returns NB_ERR_INVALID_ARG for
+ * bad parameters (checked before any CUDA call). */
+nb_status nb_create(const nb_params *params, const float *q_host, const int32_t *type_host,
+                    const int32_t *excl_off_host, const int32_t *excl_idx_host, nb_ctx **out);
+
+/* Release every resource of the context (NULL is accepted). */
+void nb_destroy(nb_ctx *ctx);
+
+/* Replace the charges with q_dev [N] (caller order, device).  Asynchronous. */
+nb_status nb_set_charges(nb_ctx *ctx, const float *q_dev, void *stream);
+
+/* Replace the Lennard-Jones tables with c6_dev / c12_dev [T*T] (device,
+ * row-major; the pair parameter is (C[a][b] + C[b][a]) / 2).  Asynchronous. */
+nb_status nb_set_lj(nb_ctx *ctx, const float *c6_dev, const float *c12_dev, void *stream);
+
+/* Grid sort (Sec. V.A, Fig. 4): bin atoms into xy columns, sort each column
+ * by z, cut it into super-cells of 64 atoms, split each super-cell 2x2x2 into
+ * 8-atom clusters (z halves, then y halves, then x halves), pad partial
+ * clusters, and compute cluster and super-cluster bounding boxes (Sec. V.D).
+ * x_dev [N*3] caller-order positions (any periodic image); box_host [3]
+ * rectangular box edges.  Each atom's periodic image offset is fixed here and
+ * reused until the next grid sort.  Allocates on first use or growth.
+ * Invalidates the pair lists. */
+nb_status nb_grid_sort(nb_ctx *ctx, const float *x_dev, const double *box_host, void *stream);
+
+/* Bounding-box cluster pair search (Sec. V.A, V.D): for every super-cluster
+ * and periodic shift, the joint list of j-clusters whose bounding box lies
+ * within rlist of any of its 8 i-cluster boxes, with the 8-bit interaction
+ * mask and exclusion bit masks; each cluster pair is listed once (Newton's
+ * third law).  Lists are split into chunks and ordered longest first (Sec. V.F).
+ * Then prunes the whole list at params.r_in into the inner list (first use,
+ * Sec. V.D).  Synchronises `stream` (list sizes are read back to size buffers
+ * and launches).  rlist must satisfy params.r_in <= rlist < L. */
+nb_status nb_pairlist_build(nb_ctx *ctx, float rlist, void *stream);
+
+/* Rolling prune (Sec. V.E): re-prune part `part` of `n_parts` interleaved
+ * parts of the outer list against r_in (rc <= r_in <= rlist), using the
+ * positions of the last nb_forces (or nb_grid_sort) call.  Keeps an
+ * interaction-mask bit iff some atom pair of that cluster pair is closer than
+ * r_in.  The outer list is unchanged.  Asynchronous; never allocates. */
+nb_status nb_prune_rolling(nb_ctx *ctx, float r_in, int part, int n_parts, void *stream);
+
+/* Forces (Sec. V.A): gathers x_dev [N*3] (caller order) into the cluster
+ * layout using the image offsets of the last grid sort, evaluates the inner
+ * list and writes f_dev [N*3] (caller order, overwritten).  flags: NB_ENERGY
+ * writes e_dev[2] = {E_LJ, E_Coulomb} (FP64, overwritten); NB_VIRIAL writes
+ * vir_dev[9] (FP64 row-major, overwritten).  Pair arithmetic and force
+ * accumulation are FP32; energies and virial are reduced in FP64.
+ * Asynchronous; never allocates; may be captured in a CUDA graph. */
+nb_status nb_forces(nb_ctx *ctx, unsigned flags, const float *x_dev, float *f_dev, double *e_dev,
+                    double *vir_dev, void *stream);
+
+/* Adjoint of nb_forces (not in the paper): for L = <gF, F> + gE*(E_LJ + E_C),
+ * recomputes every pair of the inner list at x_dev and writes gx_dev [N*3],
+ * gq_dev [N] (FP32, overwritten) and gc6_dev / gc12_dev [T*T] (FP64,
+ * overwritten).  A type pair a != b puts half of its parameter gradient in
+ * [a][b] and half in [b][a].  Asynchronous; never allocates. */
+nb_status nb_forces_vjp(nb_ctx *ctx, const float *x_dev, const float *gF_dev, double gE,
+                        float *gx_dev, float *gq_dev, double *gc6_dev, double *gc12_dev,
+                        void *stream);
+
+/* Batched evaluation of independent systems in one persistent launch
+ * (Sec. VI ensembles sharing a GPU; tail balancing of Sec. V.F).  The batch
+ * refers to (does not own) `n` contexts that already have pair lists and the
+ * same Coulomb type; it must be re-created after any of them is re-built.
+ * Allocates in nb_batch_create only. */
+nb_status nb_batch_create(nb_ctx *const *ctxs, int n, nb_batch **out);
+void nb_batch_destroy(nb_batch *batch);
+
+/* x_dev: concatenated caller-order positions of all systems (system r starts
+ * at atom offset sum_{s<r} N_s); f_dev likewise (overwritten); e_dev [n*2],
+ * vir_dev [n*9] per system.  Work items of all systems are drawn from one
+ * device queue by a persistent kernel.  Asynchronous; never allocates. */
+nb_status nb_forces_batched(nb_batch *batch, unsigned flags, const float *x_dev, float *f_dev,
+                            double *e_dev, double *vir_dev, void *stream);
+
+/* Counts over the inner list at the current positions: pairs inside rc that
+ * the kernel computes (effective interactions) and atom pairs evaluated
+ * (8x8 per set mask bit, the raw work).  Synchronises `stream`. */
+nb_status nb_count_pairs(nb_ctx *ctx, int64_t *n_within_rc, int64_t *n_evaluated, void *stream);
+
+/* Export the atom pairs the kernel would evaluate from the outer or inner list
+ * (mask bit set, both atoms real) as int64 rows (i, j, sx, sy, sz) with
+ * pair vector x_i - x_j + s*L in caller coordinates.  Writes at most cap rows
+ * to buf_host and the total to *n_total.  For tests; synchronises; allocates
+ * temporary device memory. */
+nb_status nb_debug_export_pairs(nb_ctx *ctx, int which, int64_t *buf_host, size_t cap,
+                                size_t *n_total, void *stream);
+
+/* Copy the sorted layout: perm_host [n_slots] (slot -> caller atom, -1 = pad)
+ * and, when not NULL, xq_host [n_slots*4] (x,y,z,q per slot) and
+ * bbox_host [n_clusters*8] (lo x,y,z,-, hi x,y,z,-).  For tests; synchronises. */
+nb_status nb_debug_layout(nb_ctx *ctx, int32_t *perm_host, float *xq_host, float *bbox_host,
+                          void *stream);
+
+nb_status nb_get_stats(nb_ctx *ctx, nb_stats *out);
+
+/* Tracing (not in the paper): when enabled, CUDA events are recorded on the
+ * launch stream around every force, prune, gather and adjoint kernel of this
+ * context (at most 65536 launches between reads).  Enabling creates the events
+ * (host resources); it is not allowed during stream capture. */
+nb_status nb_trace_enable(nb_ctx *ctx, int enable);
+
+/* Device time of the traced launches of one kind since the last read:
+ * *total_ms (sum of event intervals) and *n_launches.  Synchronises on the
+ * recorded events and resets the counters of that kind. */
+nb_status nb_trace_read(nb_ctx *ctx, int kind, double *total_ms, int64_t *n_launches);
+
+/* Return (and clear) the first device-side error recorded since the last
+ * call; synchronises `stream`. */
+nb_status nb_get_error(nb_ctx *ctx, void *stream);
+
+const char *nb_status_str(nb_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NB_H */

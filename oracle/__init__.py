@@ -5,5 +5,5 @@ leg import this package.  The CUDA library and its Python binding never do, and
 the two share no code.  See oracle.c for the definitions it computes.
 """
 from .oracle import (  # noqa: F401
-    build, brute, celllist, listset, pairs_within, vjp, num_threads, set_num_threads,
+    build, brute, celllist, listset, pairs_within, vjp, energy_moments, num_threads, set_num_threads,
 )

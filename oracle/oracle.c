@@ -434,6 +434,69 @@ int or_vjp(int n, const double *x, const double *q, const int *type, int T, cons
     return 0;
 }
 
+/* ----------------------------------------------- rounding-floor moments of E */
+/* Sums over unordered pairs inside rc of the squared first-order sensitivities
+ * of the pair energies to a relative perturbation of r:
+ *   m[0] = sum (r dV_LJ/dr)^2 = sum (12 C12 r^-12 - 6 C6 r^-6)^2
+ *   m[1] = sum (r dV_C/dr)^2  (f qi qj / r times the screening factor for Ewald)
+ * A relative rounding error eps in each r moves E_LJ by about eps sqrt(m[0]) (random
+ * signs), so sqrt(m)/|E| is the relative error floor of an energy summed from
+ * pair terms computed in a precision with unit roundoff eps. */
+int or_energy_moments(int n, const double *x, const double *q, const int *type, int T, const double *c6,
+                      const double *c12, const int *excl_off, const int *excl_idx, const double *box, int coulomb,
+                      double eps_r, double eps_rf, double beta, double rc, double *m) {
+    setup_t s;
+    make_setup(&s, coulomb, eps_r, eps_rf, beta, rc, T, c6, c12);
+    for (int k = 0; k < 3; k++)
+        if (!(rc < 0.5 * box[k])) return 1;
+    cells_t c;
+    int use_cells = build_cells(&c, n, x, box, rc);
+    double *acc = (double *)calloc((size_t)n * 2, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; i++) {
+        int ci[3] = {0, 0, 0};
+        if (use_cells) cell_of(&c, x + 3 * i, box, ci);
+        int span = use_cells ? 1 : 0;
+        for (int dx = -span; dx <= span; dx++)
+            for (int dy = -span; dy <= span; dy++)
+                for (int dz = -span; dz <= span; dz++) {
+                    int lo = 0, hi = n;
+                    if (use_cells) {
+                        int a = (ci[0] + dx + c.nc[0]) % c.nc[0];
+                        int b = (ci[1] + dy + c.nc[1]) % c.nc[1];
+                        int e = (ci[2] + dz + c.nc[2]) % c.nc[2];
+                        int cc = (a * c.nc[1] + b) * c.nc[2] + e;
+                        lo = c.head[cc];
+                        hi = c.head[cc + 1];
+                    }
+                    for (int p = lo; p < hi; p++) {
+                        int j = use_cells ? c.atoms[p] : p;
+                        if (j == i) continue;
+                        double d[3];
+                        min_image(x + 3 * i, x + 3 * j, box, d);
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (!(r2 < s.rc2)) continue;
+                        if (excluded(excl_off, excl_idx, i, j)) continue;
+                        pair_t pt;
+                        pair_terms(&s, r2, q[i] * q[j], pair_c(c6, T, type[i], type[j]),
+                                   pair_c(c12, T, type[i], type[j]), 0, &pt);
+                        /* r dV/dr = -phi r^2 */
+                        double slj = pt.plj * r2, sc = pt.pc * r2;
+                        acc[2 * i] += 0.5 * slj * slj;
+                        acc[2 * i + 1] += 0.5 * sc * sc;
+                    }
+                }
+    }
+    m[0] = m[1] = 0.0;
+    for (int i = 0; i < n; i++) {
+        m[0] += acc[2 * i];
+        m[1] += acc[2 * i + 1];
+    }
+    free(acc);
+    if (use_cells) free_cells(&c);
+    return 0;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -52,6 +52,8 @@ def _load():
         _lib.or_vjp.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, _d, ctypes.c_double, _d,
                                          _d, _d, _d]
+        _lib.or_energy_moments.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double,
+                                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, _d]
         _lib.or_num_threads.restype = ctypes.c_int
         _lib.or_set_num_threads.argtypes = [ctypes.c_int]
     return _lib
@@ -196,6 +198,22 @@ def vjp(s, gF, gE, x=None):
     if rc != 0:
         raise ValueError("oracle: rc must be < L/2")
     return dict(gx=gx, gq=gq, gc6=gc6, gc12=gc12)
+
+
+def energy_moments(s, x=None):
+    """(m_lj, m_c): sums over pairs inside rc of (r dV/dr)^2 for the LJ and Coulomb terms."""
+    lib = _load()
+    xx, q, ty, c6, c12, off, idx, box = _arrays(s)
+    if x is not None:
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+    m = np.zeros(2)
+    co, er, erf_, be = _coul(s)
+    rc = lib.or_energy_moments(xx.shape[0], _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d),
+                               _p(c12, _d), _p(off, _i), _p(idx, _i), _p(box, _d), co, er, erf_, be,
+                               float(s.rc), _p(m, _d))
+    if rc != 0:
+        raise ValueError("oracle: rc must be < L/2")
+    return float(m[0]), float(m[1])
 
 
 def num_threads() -> int:

@@ -1,0 +1,174 @@
+// Cluster pair force kernel (paper Sec. V.A) and the per-step gather/scatter.
+//
+// One warp evaluates one work item: a super-cluster (8 i-clusters, 64 atoms),
+// a periodic shift and a chunk of its joint j-list.  The loop order follows the
+// paper: outer loop over j-clusters, inner loop over the 8 i-clusters, with
+// whole cluster pairs skipped by the 8-bit interaction mask (a warp-uniform
+// branch, so no divergence).  Lane (ti, tj) = (lane & 7, lane >> 3) computes
+// the pairs (i-atom ti, j-atom tj) and (ti, tj + 4) of every 8x8 cluster pair,
+// so each j-atom is loaded once per entry and reused for all 8 i-clusters.
+// i-forces stay in registers for the whole item; j-forces are reduced over the
+// 8 ti lanes by shuffles at the end of each j iteration and added once per
+// j-atom.  Each pair is computed once (Newton's third law).  Exclusions and the
+// self-pair triangle come from the entry's bit masks and are applied together
+// with the cut-off test.  Pair arithmetic is FP32; energies and the virial are
+// accumulated per lane in FP32 over one item and reduced in FP64.
+//
+// Separate kernels per Coulomb type and energy/virial output (template
+// instantiations) avoid runtime conditionals in the inner loop (Sec. V.A).
+//
+// Ewald real space: phi_C = f qi qj (1/r^3 - beta^3 H(z)), V_C = f qi qj (1/r -
+// beta E(z) - erfc(beta rc)/rc) with z = beta r, evaluated with the FMA-only
+// rational approximations of ewald_rational.h plus one fast reciprocal.
+#include "nb_pair.cuh"
+
+using namespace nbk;
+
+namespace {
+
+constexpr int kFW = 4;  // warps (work items) per block
+
+template <int COUL, bool EN, bool VIR>
+__global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
+    extern __shared__ float4 s_dyn[];
+    float4 *s_lje = s_dyn;                                                  // EN only: [T*T]
+    float2 *s_lj = reinterpret_cast<float2 *>(s_dyn + (EN ? v.T * v.T : 0));  // [T*T]
+    __shared__ float4 s_xi[kFW][NB_SCA];
+    __shared__ int s_ti[kFW][NB_SCA];
+    __shared__ float s_fi[kFW][3 * NB_SCL * 32];
+    for (int t = threadIdx.x; t < v.T * v.T; t += blockDim.x) {
+        s_lj[t] = v.lj[t];
+        if (EN) s_lje[t] = v.lje[t];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int w = blockIdx.x * kFW + wib;
+    if (w >= v.n_items) return;
+    const int nj = v.inner_len[w];
+    KSum elj, ec;
+    float vr[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) vr[k] = 0.f;
+    if (nj > 0) process_item<COUL, EN, VIR>(v, w, nj, s_lj, s_lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
+    if (EN || VIR) {
+        // FP32 warp reduction; one row of 11 partial sums per work item, reduced in
+        // FP64 by the unsort kernel (no block barrier, no same-address atomics)
+        warp_reduce_outputs<EN, VIR>(elj, ec, vr);
+        if (lane < 11) {
+            double val;
+            if (lane == 0) val = (double)elj.s - (double)elj.c;
+            else if (lane == 1) val = (double)ec.s - (double)ec.c;
+            else val = (double)vr[lane - 2];
+            v.part[(size_t)w * 11 + lane] = val;
+        }
+    }
+}
+
+// Positions of the step into the cluster layout (image offsets of the last sort),
+// zeroing of the force accumulators and of the energy / virial outputs.
+__global__ void k_gather(int nslots, const int *__restrict__ perm, const float *__restrict__ x,
+                         const int *__restrict__ img, const float *__restrict__ q_s, double Lx, double Ly,
+                         double Lz, float4 *__restrict__ xq, float4 *__restrict__ fs, double *e, double *vir,
+                         int *err) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) {
+        if (e) e[0] = e[1] = 0.0;
+        if (vir)
+            for (int k = 0; k < 9; k++) vir[k] = 0.0;
+    }
+    if (s >= nslots) return;
+    fs[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int i = perm[s];
+    if (i < 0) return;
+    float p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+    int n[3];
+    img_unpack(img[i], n[0], n[1], n[2]);
+    const double L[3] = {Lx, Ly, Lz};
+    bool bad = false;
+    for (int k = 0; k < 3; k++) {
+        if (!isfinite(p[k])) {
+            bad = true;
+            p[k] = 0.f;
+        } else if (n[k] != 0) {
+            p[k] = (float)((double)p[k] - (double)n[k] * L[k]);
+        }
+    }
+    if (bad) record_error(err, NB_ERR_NONFINITE);
+    xq[s] = make_float4(p[0], p[1], p[2], q_s[s]);
+}
+
+// Forces back to caller order; each block also folds a share of the per-block
+// energy/virial partial sums into the FP64 outputs (E_C gets the Coulomb
+// constant here, the virial its factor -1/2).
+__global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__restrict__ fs, float *__restrict__ f,
+                         const double *__restrict__ part, int n_part, double coul_f, double *e, double *vir) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float4 v = fs[inv[i]];
+        f[3 * i] = v.x;
+        f[3 * i + 1] = v.y;
+        f[3 * i + 2] = v.z;
+    }
+    if (part && threadIdx.x < 11) {
+        const int k = threadIdx.x;
+        if ((k < 2 && e) || (k >= 2 && vir)) {
+            double acc = 0.0;
+            for (int r = blockIdx.x; r < n_part; r += gridDim.x) acc += part[(size_t)r * 11 + k];
+            if (k == 0) atomicAdd(&e[0], acc);
+            else if (k == 1) atomicAdd(&e[1], coul_f * acc);
+            else atomicAdd(&vir[k - 2], -0.5 * acc);
+        }
+    }
+}
+
+template <int COUL, bool EN, bool VIR>
+void launch_forces_t(const SysView &v, cudaStream_t st) {
+    size_t smem = (sizeof(float2) + (EN ? sizeof(float4) : 0)) * v.T * v.T;
+    k_forces<COUL, EN, VIR><<<(v.n_items + kFW - 1) / kFW, kFW * 32, smem, st>>>(v);
+}
+
+}  // namespace
+
+nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cudaStream_t st) {
+    const int ns = c->S_host * NB_SCA;
+    NbTraceScope tr(c, NB_TRACE_GATHER, st);
+    c->n_launches++;
+    k_gather<<<(ns + 255) / 256, 256, 0, st>>>(ns, c->perm, x, c->img, c->q_s, c->box[0], c->box[1],
+                                                c->box[2], c->xq, c->fs, e, vir, c->err);
+    NB_CUDA_TRY(cudaGetLastError());
+    return NB_OK;
+}
+
+void nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, cudaStream_t st) {
+    const bool en = flags & NB_ENERGY, vi = flags & NB_VIRIAL;
+    if (coulomb == NB_COULOMB_RF) {
+        if (en && vi) launch_forces_t<NB_COULOMB_RF, true, true>(v, st);
+        else if (en) launch_forces_t<NB_COULOMB_RF, true, false>(v, st);
+        else if (vi) launch_forces_t<NB_COULOMB_RF, false, true>(v, st);
+        else launch_forces_t<NB_COULOMB_RF, false, false>(v, st);
+    } else {
+        if (en && vi) launch_forces_t<NB_COULOMB_EWALD, true, true>(v, st);
+        else if (en) launch_forces_t<NB_COULOMB_EWALD, true, false>(v, st);
+        else if (vi) launch_forces_t<NB_COULOMB_EWALD, false, true>(v, st);
+        else launch_forces_t<NB_COULOMB_EWALD, false, false>(v, st);
+    }
+}
+
+int nb_force_blocks(int n_items) { return n_items; }  // rows of per-item partial sums
+
+nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, double *vir, cudaStream_t st) {
+    const bool red = flags & (NB_ENERGY | NB_VIRIAL);
+    SysView v = nb_make_view(c, c->fs, (flags & NB_ENERGY) ? e : nullptr, (flags & NB_VIRIAL) ? vir : nullptr);
+    if (v.n_items > 0) {
+        NbTraceScope tr(c, NB_TRACE_FORCES, st);
+        nb_dispatch_forces(v, c->coulomb, flags, st);
+        c->n_launches++;
+    }
+    const int nb = (c->N + 255) / 256;
+    c->n_launches++;
+    k_unsort<<<nb, 256, 0, st>>>(c->N, c->inv, c->fs, f, (red && v.n_items > 0) ? c->part : nullptr,
+                                 nb_force_blocks(v.n_items), 138.935458 / c->eps_r,
+                                 (flags & NB_ENERGY) ? e : nullptr, (flags & NB_VIRIAL) ? vir : nullptr);
+    NB_CUDA_TRY(cudaGetLastError());
+    return NB_OK;
+}

@@ -1,0 +1,318 @@
+// Device code shared by the plain and the batched force kernels: the Ewald
+// rational approximations, the pair interaction and the per-work-item loop of
+// the cluster pair algorithm (paper Sec. V.A).
+#pragma once
+#include "ewald_rational.h"
+#include "nb_internal.cuh"
+
+namespace nbk {
+
+static_assert(NB_EW_ZMAX == (float)NB_EW_ZMAX_D, "Ewald fit range");
+
+
+__device__ __forceinline__ float ew_h(float s) {
+    float p = fmaf(NB_EW_HP6, s, NB_EW_HP5);
+    p = fmaf(p, s, NB_EW_HP4);
+    p = fmaf(p, s, NB_EW_HP3);
+    p = fmaf(p, s, NB_EW_HP2);
+    p = fmaf(p, s, NB_EW_HP1);
+    p = fmaf(p, s, NB_EW_HP0);
+    float q = fmaf(NB_EW_HQ5, s, NB_EW_HQ4);
+    q = fmaf(q, s, NB_EW_HQ3);
+    q = fmaf(q, s, NB_EW_HQ2);
+    q = fmaf(q, s, NB_EW_HQ1);
+    q = fmaf(q, s, 1.0f);
+    return __fdividef(p, q);
+}
+
+__device__ __forceinline__ float ew_e(float s) {
+    float p = fmaf(NB_EW_EP5, s, NB_EW_EP4);
+    p = fmaf(p, s, NB_EW_EP3);
+    p = fmaf(p, s, NB_EW_EP2);
+    p = fmaf(p, s, NB_EW_EP1);
+    p = fmaf(p, s, NB_EW_EP0);
+    float q = fmaf(NB_EW_EQ5, s, NB_EW_EQ4);
+    q = fmaf(q, s, NB_EW_EQ3);
+    q = fmaf(q, s, NB_EW_EQ2);
+    q = fmaf(q, s, NB_EW_EQ1);
+    q = fmaf(q, s, 1.0f);
+    return __fdividef(p, q);
+}
+
+// erfc(z) = exp(-z^2) X(z), X the scaled complementary error function (rational in z/ZMAX)
+__device__ __forceinline__ float ew_erfc(float z) {
+    const float t = z * (1.0f / NB_EW_ZMAX);
+    float p = fmaf(NB_EW_XP4, t, NB_EW_XP3);
+    p = fmaf(p, t, NB_EW_XP2);
+    p = fmaf(p, t, NB_EW_XP1);
+    p = fmaf(p, t, NB_EW_XP0);
+    float q = fmaf(NB_EW_XQ4, t, NB_EW_XQ3);
+    q = fmaf(q, t, NB_EW_XQ2);
+    q = fmaf(q, t, NB_EW_XQ1);
+    q = fmaf(q, t, 1.0f);
+    return __expf(-z * z) * __fdividef(p, q);
+}
+
+// Periodic shift of a work item split between the two sides of each pair so
+// that every shifted coordinate stays exact.  For shift s (per axis) the pair
+// vector is x_i - x_j + s L.  On an axis with s = -1 the i-atoms lie near the
+// upper face and x_i - L is exact (Sterbenz); with s = +1 the j-atoms lie near
+// the upper face and x_j - L is exact.  Adding L to a coordinate near 0
+// instead would round away the low bits of L and bias every such pair alike.
+// L = Lhi + Llo (float pair); the Llo parts are added after the exact step.
+struct ShiftSplit {
+    float ihi[3], ilo[3];  // x_i' = (x_i + ihi) + ilo
+    float jhi[3], jlo[3];  // x_j' = (x_j - jhi) - jlo
+    bool jshift;
+};
+
+__device__ __forceinline__ ShiftSplit make_shift(int sidx, const float *Lhi, const float *Llo) {
+    ShiftSplit r;
+    int s[3];
+    shift_of(sidx, s[0], s[1], s[2]);
+    r.jshift = false;
+    for (int k = 0; k < 3; k++) {
+        r.ihi[k] = s[k] < 0 ? -Lhi[k] : 0.f;
+        r.ilo[k] = s[k] < 0 ? -Llo[k] : 0.f;
+        r.jhi[k] = s[k] > 0 ? Lhi[k] : 0.f;
+        r.jlo[k] = s[k] > 0 ? Llo[k] : 0.f;
+        r.jshift |= s[k] > 0;
+    }
+    return r;
+}
+
+__device__ __forceinline__ float4 shift_i(float4 p, const ShiftSplit &sh) {
+    p.x = (p.x + sh.ihi[0]) + sh.ilo[0];
+    p.y = (p.y + sh.ihi[1]) + sh.ilo[1];
+    p.z = (p.z + sh.ihi[2]) + sh.ilo[2];
+    return p;
+}
+
+__device__ __forceinline__ float4 shift_j(float4 p, const ShiftSplit &sh) {
+    p.x = (p.x - sh.jhi[0]) - sh.jlo[0];
+    p.y = (p.y - sh.jhi[1]) - sh.jlo[1];
+    p.z = (p.z - sh.jhi[2]) - sh.jlo[2];
+    return p;
+}
+
+// Compensated (Kahan) accumulation of the per-entry energy subtotals: the
+// energy totals of small systems are sums of many terms that nearly cancel, so
+// the running-sum rounding of a plain FP32 accumulator would dominate.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    // merge another compensated sum (error-free two-sum of the leading parts)
+    __device__ __forceinline__ void merge(float s2, float c2) {
+        const float t = s + s2;
+        const float bp = t - s;
+        const float err = (s - (t - bp)) + (s2 - bp);
+        s = t;
+        c = c + c2 - err;
+    }
+};
+
+// One pair: returns the scalar force phi (force on i = phi * d), adds energies.
+// Force-only kernels get qi pre-multiplied by the Coulomb constant f; energy
+// kernels get the raw charge and apply f to the force here and to the energy
+// once, in FP64, after the reduction (a rounded f would bias every pair alike).
+template <int COUL, bool EN>
+__device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__restrict__ ljt,
+                                          const float4 *__restrict__ lje, float3 d, float qi, float qj, int tpair,
+                                          bool bit, float &elj, float &ec) {
+    float r2 = fmaf(d.z, d.z, fmaf(d.y, d.y, d.x * d.x));
+    const bool in = bit && (r2 < v.rc2);
+    r2 = in ? r2 : v.rc2;
+    float rinv = rsqrtf(r2);
+    if (EN) rinv = rsqrt_refine(r2, rinv);
+    const float rinv2 = rinv * rinv;
+    const float rinv6 = rinv2 * rinv2 * rinv2;
+    const float2 lj = ljt[tpair];  // (6 C6, 12 C12)
+    const float flj = rinv6 * fmaf(lj.y, rinv6, -lj.x);
+    const float qq = qi * qj;
+    float fc;
+    if (COUL == NB_COULOMB_RF) {
+        fc = qq * fmaf(rinv, rinv2, -2.0f * v.k_rf);
+    } else {
+        fc = qq * fmaf(rinv, rinv2, -v.ew_beta3 * ew_h(r2 * v.ew_s));
+    }
+    if (EN) fc *= v.coul_f;
+    float phi = fmaf(flj, rinv2, fc);
+    phi = in ? phi : 0.f;
+    if (EN) {
+        const float4 le = lje[tpair];  // (C6, C12, C12/rc^12 - C6/rc^6, -)
+        const float vlj = fmaf(rinv6, fmaf(le.y, rinv6, -le.x), -le.z);
+        float vc;
+        if (COUL == NB_COULOMB_RF) {
+            // 1/r as a float pair (rinv + rlo) from the exact residual 1 - r2 rinv^2;
+            // (rinv - c_rf) is then exact near the cut-off, where the terms cancel
+            const float t_hi = rinv * rinv;
+            const float t_lo = fmaf(rinv, rinv, -t_hi);
+            const float e = fmaf(-r2, t_hi, 1.0f) - r2 * t_lo;
+            const float rlo = 0.5f * rinv * e;
+            vc = (rinv - v.c_rf) + (fmaf(v.k_rf, r2, -v.c_rf_lo) + rlo);
+        } else {
+            // CUDA's erfcf: measured against FP64 erfc it has the smallest bias of the
+            // variants tried (the energy totals of water sum 10^5-10^7 cancelling terms)
+            vc = fmaf(erfcf(v.ew_beta * (r2 * rinv)), rinv, -v.ew_shift);
+        }
+        elj += in ? vlj : 0.f;
+        ec += in ? qq * vc : 0.f;
+    }
+    return phi;
+}
+
+// Evaluate work item w (nj > 0 inner entries) with one warp.  s_xi / s_ti are
+// this warp's 64-entry staging arrays and s_fi its i-force accumulators
+// ([8 clusters][3][32 lanes] floats, conflict-free); ljt / lje the pair tables
+// (shared or global memory).  Forces are added to v.f; energies and the virial
+// sum of r (x) F go to the caller's per-lane accumulators.  The i-cluster loop
+// walks the set bits of the interaction mask (a warp-uniform loop) and is not
+// unrolled, so the kernel stays small enough for the instruction cache and the
+// i-forces of the 8 clusters live in shared memory rather than in registers.
+template <int COUL, bool EN, bool VIR>
+__device__ __forceinline__ void process_item(const SysView &v, int w, int nj, const float2 *ljt, const float4 *lje,
+                                             float4 *s_xi, int *s_ti, float *s_fi, KSum &elj, KSum &ec,
+                                             float (&vr)[9]) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int4 it = v.items[w];
+    const int si = it.x, j0 = it.z;
+    const ShiftSplit sh = make_shift(it.y, v.box_hi, v.box_lo);
+    for (int h = 0; h < 2; h++) {
+        const int at = lane + 32 * h;
+        float4 p = shift_i(v.xq[si * NB_SCA + at], sh);
+        if (!EN) p.w *= v.coul_f;
+        s_xi[at] = p;
+        s_ti[at] = v.type[si * NB_SCA + at] * v.T;
+    }
+#pragma unroll
+    for (int k = 0; k < 3 * NB_SCL; k++) s_fi[k * 32 + lane] = 0.f;
+    __syncwarp();
+    const int ti = lane & 7, tj = lane >> 3;
+    float4 org = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (VIR) org = s_xi[0];
+
+    for (int e = 0; e < nj; e++) {
+        const int2 ent = v.cj[j0 + e];
+        const int cj = ent.x, mg = ent.y >> 8;
+        int im = ent.y & 0xff;
+        float4 xj0 = v.xq[cj * NB_CL + tj], xj1 = v.xq[cj * NB_CL + tj + 4];
+        if (sh.jshift) {
+            xj0 = shift_j(xj0, sh);
+            xj1 = shift_j(xj1, sh);
+        }
+        const int tj0 = v.type[cj * NB_CL + tj], tj1 = v.type[cj * NB_CL + tj + 4];
+        float f0x = 0.f, f0y = 0.f, f0z = 0.f, f1x = 0.f, f1y = 0.f, f1z = 0.f;
+        float elj_e = 0.f, ec_e = 0.f;
+#pragma unroll 1
+        while (im) {
+            const int k = __ffs(im) - 1;
+            im &= im - 1;
+            bool b0 = true, b1 = true;
+            if (mg) {
+                const unsigned long long m = v.masks[(size_t)(mg - 1) * 8 + k];
+                b0 = (m >> (ti * 8 + tj)) & 1ull;
+                b1 = (m >> (ti * 8 + tj + 4)) & 1ull;
+            }
+            const float4 xi = s_xi[k * NB_CL + ti];
+            const int tio = s_ti[k * NB_CL + ti];
+            const float3 d0 = make_float3(xi.x - xj0.x, xi.y - xj0.y, xi.z - xj0.z);
+            const float3 d1 = make_float3(xi.x - xj1.x, xi.y - xj1.y, xi.z - xj1.z);
+            const float p0 = pair_phi<COUL, EN>(v, ljt, lje, d0, xi.w, xj0.w, tio + tj0, b0, elj_e, ec_e);
+            const float p1 = pair_phi<COUL, EN>(v, ljt, lje, d1, xi.w, xj1.w, tio + tj1, b1, elj_e, ec_e);
+            const float ax = p0 * d0.x, ay = p0 * d0.y, az = p0 * d0.z;
+            const float bx = p1 * d1.x, by = p1 * d1.y, bz = p1 * d1.z;
+            float *fk = s_fi + k * 96 + lane;
+            fk[0] += ax + bx;
+            fk[32] += ay + by;
+            fk[64] += az + bz;
+            f0x -= ax;
+            f0y -= ay;
+            f0z -= az;
+            f1x -= bx;
+            f1y -= by;
+            f1z -= bz;
+        }
+        if (EN) {
+            elj.add(elj_e);
+            ec.add(ec_e);
+        }
+        if (VIR) {
+            const float ux = xj0.x - org.x, uy = xj0.y - org.y, uz = xj0.z - org.z;
+            const float wx = xj1.x - org.x, wy = xj1.y - org.y, wz = xj1.z - org.z;
+            vr[0] += ux * f0x + wx * f1x;
+            vr[1] += ux * f0y + wx * f1y;
+            vr[2] += ux * f0z + wx * f1z;
+            vr[3] += uy * f0x + wy * f1x;
+            vr[4] += uy * f0y + wy * f1y;
+            vr[5] += uy * f0z + wy * f1z;
+            vr[6] += uz * f0x + wz * f1x;
+            vr[7] += uz * f0y + wz * f1y;
+            vr[8] += uz * f0z + wz * f1z;
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            f0x += __shfl_xor_sync(full, f0x, o);
+            f0y += __shfl_xor_sync(full, f0y, o);
+            f0z += __shfl_xor_sync(full, f0z, o);
+            f1x += __shfl_xor_sync(full, f1x, o);
+            f1y += __shfl_xor_sync(full, f1y, o);
+            f1z += __shfl_xor_sync(full, f1z, o);
+        }
+        if (ti == 0) {
+            atomicAdd(&v.f[cj * NB_CL + tj], make_float4(f0x, f0y, f0z, 0.f));
+            atomicAdd(&v.f[cj * NB_CL + tj + 4], make_float4(f1x, f1y, f1z, 0.f));
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < NB_SCL; k++) {
+        float fx = s_fi[k * 96 + lane], fy = s_fi[k * 96 + 32 + lane], fz = s_fi[k * 96 + 64 + lane];
+        if (VIR) {
+            const float4 xi = s_xi[k * NB_CL + ti];
+            const float ux = xi.x - org.x, uy = xi.y - org.y, uz = xi.z - org.z;
+            vr[0] += ux * fx;
+            vr[1] += ux * fy;
+            vr[2] += ux * fz;
+            vr[3] += uy * fx;
+            vr[4] += uy * fy;
+            vr[5] += uy * fz;
+            vr[6] += uz * fx;
+            vr[7] += uz * fy;
+            vr[8] += uz * fz;
+        }
+        fx += __shfl_xor_sync(full, fx, 8);
+        fy += __shfl_xor_sync(full, fy, 8);
+        fz += __shfl_xor_sync(full, fz, 8);
+        fx += __shfl_xor_sync(full, fx, 16);
+        fy += __shfl_xor_sync(full, fy, 16);
+        fz += __shfl_xor_sync(full, fz, 16);
+        if (tj == 0) atomicAdd(&v.f[si * NB_SCA + k * NB_CL + ti], make_float4(fx, fy, fz, 0.f));
+    }
+}
+
+// Warp reduction of the per-lane energy/virial accumulators (FP32; compensated
+// for the energies).  Every lane ends with the warp total.
+template <bool EN, bool VIR>
+__device__ __forceinline__ void warp_reduce_outputs(KSum &elj, KSum &ec, float (&vr)[9]) {
+    const unsigned full = 0xffffffffu;
+    for (int o = 16; o > 0; o >>= 1) {
+        if (EN) {
+            const float a = __shfl_xor_sync(full, elj.s, o), ac = __shfl_xor_sync(full, elj.c, o);
+            const float b = __shfl_xor_sync(full, ec.s, o), bc = __shfl_xor_sync(full, ec.c, o);
+            elj.merge(a, ac);
+            ec.merge(b, bc);
+        }
+        if (VIR) {
+#pragma unroll
+            for (int k = 0; k < 9; k++) vr[k] += __shfl_xor_sync(full, vr[k], o);
+        }
+    }
+}
+
+}  // namespace nbk

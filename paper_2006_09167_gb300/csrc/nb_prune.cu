@@ -1,0 +1,218 @@
+// Atom-distance pruning of the cluster pair list (paper Sec. V.D) and the
+// dual-list rolling prune (Sec. V.E), plus list diagnostics.
+//
+// The outer list (bounding-box search at rlist) is kept; the inner list holds,
+// for each work item, the outer entries whose interaction-mask bits survive an
+// atom-pair distance test at r_in.  A bit k survives iff some atom pair of
+// i-cluster k and the j-cluster is closer than r_in at the current positions.
+// Rolling: one call prunes the items with index = part (mod n_parts), so the
+// whole outer list is re-pruned once every n_parts calls.
+#include "nb_pair.cuh"
+
+using namespace nbk;
+
+namespace {
+
+constexpr int kPW = 4;  // warps per block
+
+struct PruneArgs {
+    int n_items, part, n_parts;
+    const int4 *items;
+    const int2 *cj_outer;
+    const float4 *xq;
+    float Lhi[3], Llo[3];
+    float rin2;
+    int2 *cj_inner;
+    int *inner_len;
+};
+
+__global__ void __launch_bounds__(kPW * 32) k_prune(PruneArgs a) {
+    __shared__ float4 s_xi[kPW][NB_SCA];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long w = (long long)blockIdx.x * kPW + wib;
+    const long long item = a.part + w * a.n_parts;
+    if (item >= a.n_items) return;
+    const int4 it = a.items[item];
+    const int si = it.x, sidx = it.y, j0 = it.z, len = it.w;
+    const ShiftSplit sh = make_shift(sidx, a.Lhi, a.Llo);
+    for (int h = 0; h < 2; h++) {
+        int at = lane + 32 * h;
+        s_xi[wib][at] = shift_i(a.xq[si * NB_SCA + at], sh);
+    }
+    __syncwarp();
+    const int ti = lane & 7, tj = lane >> 3;
+    int cnt = 0;
+    for (int e = 0; e < len; e++) {
+        const int2 ent = a.cj_outer[j0 + e];
+        const int cj = ent.x, im = ent.y & 0xff;
+        const float4 xj0 = shift_j(a.xq[cj * NB_CL + tj], sh), xj1 = shift_j(a.xq[cj * NB_CL + tj + 4], sh);
+        int kept = 0;
+#pragma unroll
+        for (int k = 0; k < NB_SCL; k++) {
+            if (im & (1 << k)) {
+                const float4 xi = s_xi[wib][k * NB_CL + ti];
+                float dx = xi.x - xj0.x, dy = xi.y - xj0.y, dz = xi.z - xj0.z;
+                float r2a = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                dx = xi.x - xj1.x;
+                dy = xi.y - xj1.y;
+                dz = xi.z - xj1.z;
+                float r2b = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                if (__any_sync(0xffffffffu, r2a < a.rin2 || r2b < a.rin2)) kept |= 1 << k;
+            }
+        }
+        if (kept) {
+            if (lane == 0) a.cj_inner[j0 + cnt] = make_int2(cj, (ent.y & ~0xff) | kept);
+            cnt++;
+        }
+    }
+    if (lane == 0) a.inner_len[item] = cnt;
+}
+
+// Counts over the inner list: pairs inside rc that are computed, and 64 per mask bit.
+__global__ void __launch_bounds__(kPW * 32)
+    k_count(int n_items, const int4 *items, const int *inner_len, const int2 *cj, const unsigned long long *masks,
+            const float4 *xq, float Lhi0, float Lhi1, float Lhi2, float Llo0, float Llo1, float Llo2, float rc2,
+            unsigned long long *out) {
+    __shared__ float4 s_xi[kPW][NB_SCA];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int item = blockIdx.x * kPW + wib;
+    if (item >= n_items) return;
+    const float Lhi[3] = {Lhi0, Lhi1, Lhi2}, Llo[3] = {Llo0, Llo1, Llo2};
+    const int4 it = items[item];
+    const int len = inner_len[item];
+    const ShiftSplit sh = make_shift(it.y, Lhi, Llo);
+    for (int h = 0; h < 2; h++) {
+        int at = lane + 32 * h;
+        s_xi[wib][at] = shift_i(xq[it.x * NB_SCA + at], sh);
+    }
+    __syncwarp();
+    const int ti = lane & 7, tj = lane >> 3;
+    unsigned long long within = 0, evald = 0;
+    for (int e = 0; e < len; e++) {
+        const int2 ent = cj[it.z + e];
+        const int c = ent.x, im = ent.y & 0xff, mg = ent.y >> 8;
+        for (int k = 0; k < NB_SCL; k++) {
+            if (!(im & (1 << k))) continue;
+            evald += 2;
+            const unsigned long long m = mg ? masks[(size_t)(mg - 1) * 8 + k] : ~0ull;
+            const float4 xi = s_xi[wib][k * NB_CL + ti];
+            for (int h = 0; h < 2; h++) {
+                const float4 xj = shift_j(xq[c * NB_CL + tj + 4 * h], sh);
+                float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+                float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                bool bit = (m >> (ti * 8 + tj + 4 * h)) & 1ull;
+                within += (bit && r2 < rc2) ? 1 : 0;
+            }
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        within += __shfl_xor_sync(0xffffffffu, within, d);
+        evald += __shfl_xor_sync(0xffffffffu, evald, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&out[0], within);
+        atomicAdd(&out[1], evald);
+    }
+}
+
+// Export of atom pairs (caller indices and image shifts) for set mask bits.
+__global__ void __launch_bounds__(kPW * 32)
+    k_export(int n_items, const int4 *items, const int *inner_len, const int2 *cj,
+             const unsigned long long *masks, const int *perm, const int *img, long long cap,
+             long long *buf, unsigned long long *count) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int item = blockIdx.x * kPW + wib;
+    if (item >= n_items) return;
+    const int4 it = items[item];
+    const int len = inner_len ? inner_len[item] : it.w;
+    int sx, sy, sz;
+    shift_of(it.y, sx, sy, sz);
+    for (int e = 0; e < len; e++) {
+        const int2 ent = cj[it.z + e];
+        const int c = ent.x, im = ent.y & 0xff, mg = ent.y >> 8;
+        for (int k = 0; k < NB_SCL; k++) {
+            if (!(im & (1 << k))) continue;
+            const unsigned long long m = mg ? masks[(size_t)(mg - 1) * 8 + k] : ~0ull;
+            for (int h = 0; h < 2; h++) {
+                const int p = lane + 32 * h;  // p = 8*a + b
+                const int ia = p >> 3, jb = p & 7;
+                if (!((m >> p) & 1ull)) continue;
+                const int i = perm[it.x * NB_SCA + k * NB_CL + ia];
+                const int j = perm[c * NB_CL + jb];
+                if (i < 0 || j < 0) continue;
+                int ix, iy, iz, jx, jy, jz;
+                img_unpack(img[i], ix, iy, iz);
+                img_unpack(img[j], jx, jy, jz);
+                unsigned long long slot = atomicAdd(count, 1ull);
+                if ((long long)slot < cap) {
+                    long long *o = buf + 5 * slot;
+                    o[0] = i;
+                    o[1] = j;
+                    o[2] = sx - ix + jx;
+                    o[3] = sy - iy + jy;
+                    o[4] = sz - iz + jz;
+                }
+            }
+        }
+    }
+}
+
+void box_split(const nb_ctx *c, float *hi, float *lo) {
+    for (int k = 0; k < 3; k++) {
+        hi[k] = (float)c->box[k];
+        lo[k] = (float)(c->box[k] - (double)hi[k]);
+    }
+}
+
+}  // namespace
+
+nb_status nb_launch_prune(nb_ctx *c, float r_in, int part, int n_parts, cudaStream_t st) {
+    if (c->n_items == 0) return NB_OK;
+    PruneArgs a;
+    a.n_items = c->n_items;
+    a.part = part;
+    a.n_parts = n_parts;
+    a.items = c->items;
+    a.cj_outer = c->cj_outer;
+    a.xq = c->xq;
+    box_split(c, a.Lhi, a.Llo);
+    // a hair wider than r_in so that FP32 rounding never drops a pair the FP64 definition keeps
+    float re = r_in * (1.0f + 2e-6f);
+    a.rin2 = re * re;
+    a.cj_inner = c->cj_inner;
+    a.inner_len = c->inner_len;
+    long long nw = (c->n_items - part + n_parts - 1) / n_parts;
+    if (nw <= 0) return NB_OK;
+    NbTraceScope tr(c, NB_TRACE_PRUNE, st);
+    c->n_launches++;
+    k_prune<<<(unsigned)((nw + kPW - 1) / kPW), kPW * 32, 0, st>>>(a);
+    NB_CUDA_TRY(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status nb_launch_count(nb_ctx *c, cudaStream_t st) {
+    NB_CUDA_TRY(cudaMemsetAsync(c->diag, 0, 2 * sizeof(long long), st));
+    if (c->n_items == 0) return NB_OK;
+    float hi[3], lo[3];
+    box_split(c, hi, lo);
+    float rc = (float)c->rc;
+    c->n_launches++;
+    k_count<<<(c->n_items + kPW - 1) / kPW, kPW * 32, 0, st>>>(
+        c->n_items, c->items, c->inner_len, c->cj_inner, c->masks, c->xq, hi[0], hi[1], hi[2], lo[0], lo[1],
+        lo[2], rc * rc, reinterpret_cast<unsigned long long *>(c->diag));
+    NB_CUDA_TRY(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status nb_launch_export(nb_ctx *c, int which, long long *buf, long long cap, long long *count,
+                           cudaStream_t st) {
+    NB_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(long long), st));
+    if (c->n_items == 0) return NB_OK;
+    const bool inner = which == NB_LIST_INNER;
+    c->n_launches++;
+    k_export<<<(c->n_items + kPW - 1) / kPW, kPW * 32, 0, st>>>(
+        c->n_items, c->items, inner ? c->inner_len : nullptr, inner ? c->cj_inner : c->cj_outer, c->masks,
+        c->perm, c->img, cap, buf, reinterpret_cast<unsigned long long *>(count));
+    NB_CUDA_TRY(cudaGetLastError());
+    return NB_OK;
+}

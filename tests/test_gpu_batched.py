@@ -1,0 +1,91 @@
+"""Batched persistent kernel (nb_forces_batched) against per-system nb_forces and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_09167_gb300 import synth
+from helpers import TOL_F, energy_tolerances, rel, rms_rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_09167_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def replicas():
+    return synth.replica_set(n_rep=12, seed=9, mol_min=300, mol_max=3000)
+
+
+def build_all(api, systems):
+    ctxs, xs = [], []
+    for s in systems:
+        c = api.NbContext.from_system(s)
+        x = torch.tensor(s.x, device="cuda")
+        c.build(x, s.box)
+        ctxs.append(c)
+        xs.append(x)
+    return ctxs, xs
+
+
+def test_batched_equals_plain(api, replicas):
+    ctxs, xs = build_all(api, replicas)
+    plain = [c.forces(x, energy=True, virial=True) for c, x in zip(ctxs, xs)]
+    b = api.NbBatch(ctxs)
+    xcat = torch.cat(xs).contiguous()
+    f = torch.empty_like(xcat)
+    e = torch.empty(2 * len(ctxs), dtype=torch.float64, device="cuda")
+    w = torch.empty(9 * len(ctxs), dtype=torch.float64, device="cuda")
+    b.nb_forces_batched(api.NB_ENERGY | api.NB_VIRIAL, xcat, f, e, w)
+    torch.cuda.synchronize()
+    off = b.offsets
+    for r, (fp, ep, wp) in enumerate(plain):
+        fb = f[off[r]:off[r + 1]].cpu().numpy()
+        assert rms_rel(fb, fp.cpu().numpy()) < 1e-6
+        assert rel(e[2 * r].item(), ep[0].item()) < 1e-9
+        assert rel(e[2 * r + 1].item(), ep[1].item()) < 1e-9
+        wb = w[9 * r:9 * r + 9].cpu().numpy()
+        assert np.abs(wb - wp.cpu().numpy().ravel()).max() <= 1e-6 * np.abs(wp.cpu().numpy()).max()
+    for c in ctxs:
+        assert c.nb_get_error() == 0
+
+
+def test_batched_oracle_parity_and_graph_replay(api, replicas):
+    ctxs, xs = build_all(api, replicas)
+    b = api.NbBatch(ctxs)
+    xcat = torch.cat(xs).contiguous()
+    f = torch.empty_like(xcat)
+    e = torch.empty(2 * len(ctxs), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.nb_forces_batched(api.NB_ENERGY, xcat, f, e)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.nb_forces_batched(api.NB_ENERGY, xcat, f, e)
+    f.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    off = b.offsets
+    for r in (0, 5, 11):
+        sysr = replicas[r]
+        ref = oracle.celllist(sysr)
+        tol_lj, tol_c = energy_tolerances(sysr, ref)
+        assert rms_rel(f[off[r]:off[r + 1]].cpu().numpy(), ref["F"]) < TOL_F
+        assert rel(e[2 * r].item(), ref["E_lj"]) < tol_lj
+        assert rel(e[2 * r + 1].item(), ref["E_c"]) < tol_c
+
+
+def test_batch_requires_lists(api, replicas):
+    c = api.NbContext.from_system(replicas[0])
+    with pytest.raises(api.NbError) as ei:
+        api.NbBatch([c])
+    assert ei.value.status == 3
