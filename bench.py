@@ -51,6 +51,12 @@ FLOPS_PER_PAIR = {
 }
 
 
+# DRAM bytes (read + write) of one k_forces<Ewald, energy, virial> launch on the
+# 96k box from the ncu capture summarised in profiles/k_forces_spce_water_96k.md;
+# set to None whenever the force kernel changes until it is captured again.
+FORCE_KERNEL_DRAM_BYTES = 7427584
+
+
 def rank_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -390,7 +396,7 @@ def main_ours(args):
                 "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": int(res["launches"]),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": FORCE_KERNEL_DRAM_BYTES,
                      "kernel": "k_forces<Ewald, energy, virial>", "avg_launch_ms": fk_avg_ms,
                      "effective_pairs_per_launch": int(res["n_eff"]), "evaluated_pairs_per_launch": int(res["n_raw"]),
                      "flops_per_effective_pair": FLOPS_PER_PAIR[("ewald", "FEV")],
