@@ -220,6 +220,37 @@ nb_status nb_get_error(nb_ctx *ctx, void *stream);
 
 const char *nb_status_str(nb_status s);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free evaluation of one small system.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory, such
+ * as code running while a stream is captured into a CUDA graph (cudaMalloc is
+ * not permitted there), code whose device memory belongs to another allocator,
+ * and latency-critical code that cannot risk the device synchronisation
+ * cudaMalloc/cudaFree may cause.  It needs no context and no pair list: all
+ * pairs of the system are evaluated with the same pair interactions as
+ * nb_forces (inputs: params (rlist and r_in are ignored), x_dev [N*3], q_dev [N],
+ * type_dev [N], optional device exclusion CSR excl_off_dev [N+1] /
+ * excl_idx_dev (both NULL for none, at most 16 partners per atom), box_host [3];
+ * outputs as nb_forces: f_dev [N*3] overwritten, e_dev [2] with NB_ENERGY,
+ * vir_dev [9] with NB_VIRIAL).
+ *
+ * Its scratch is a file-scope static device array of about 410 KB that every
+ * GPU loading the library holds until the process exits.  Limits: N <=
+ * NB_NOALLOC_MAX_ATOMS and T <= NB_NOALLOC_MAX_TYPES; larger sizes return
+ * NB_ERR_CAPACITY before any work is enqueued.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array (each call overwrites what it reads, nothing has to start at
+ * zero), so calls whose work overlaps on the GPU -- e.g. on two streams
+ * without ordering -- race and give wrong results; order them on one stream.
+ * Never allocates.  Intended for small systems: the work is O(N^2). */
+#define NB_NOALLOC_MAX_ATOMS 16384
+#define NB_NOALLOC_MAX_TYPES 8
+nb_status nb_forces_small_noalloc(const nb_params *params, const float *x_dev, const float *q_dev,
+                                  const int32_t *type_dev, const int32_t *excl_off_dev,
+                                  const int32_t *excl_idx_dev, const double *box_host, unsigned flags,
+                                  float *f_dev, double *e_dev, double *vir_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

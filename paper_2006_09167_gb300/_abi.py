@@ -34,7 +34,10 @@ EXPORTED = [
     "nb_prune_rolling", "nb_forces", "nb_forces_vjp", "nb_batch_create", "nb_batch_destroy",
     "nb_forces_batched", "nb_count_pairs", "nb_debug_export_pairs", "nb_debug_layout",
     "nb_get_stats", "nb_get_error", "nb_status_str", "nb_trace_enable", "nb_trace_read",
+    "nb_forces_small_noalloc",
 ]
+NB_NOALLOC_MAX_ATOMS = 16384
+NB_NOALLOC_MAX_TYPES = 8
 NB_TRACE_FORCES = 0
 NB_TRACE_PRUNE = 1
 NB_TRACE_GATHER = 2
@@ -102,6 +105,8 @@ def load(path: str = LIB_PATH):
     lib.nb_get_error.argtypes = [vp, vp]
     lib.nb_trace_enable.argtypes = [vp, ctypes.c_int]
     lib.nb_trace_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p]
+    lib.nb_forces_small_noalloc.argtypes = [ctypes.POINTER(NbParams), vp, vp, vp, vp, vp,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.c_uint, vp, vp, vp, vp]
     lib.nb_status_str.argtypes = [ctypes.c_int]
     lib.nb_status_str.restype = ctypes.c_char_p
     for name in EXPORTED:
