@@ -62,6 +62,25 @@ def rank_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def replica_shard(n_systems: int, rank: int, world: int):
+    """Independent systems owned by one rank (round robin; no data exchange between ranks)."""
+    return list(range(rank, n_systems, world))
+
+
+def workload_seed(rank: int) -> int:
+    """Each rank evaluates its own copy of the workload, generated from its own seed."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(values, device):
+    """Element-wise maximum over ranks of a list of floats (timing only; not on the data path)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling while the timed region runs."""
 
@@ -140,7 +159,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_2006_09167_gb300 import api, synth
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    s = synth.water_96k(seed=2 + 1000 * rank)
+    s = synth.water_96k(seed=workload_seed(rank))
     ctx = api.NbContext.from_system(s)
     x0 = torch.tensor(s.x, device=dev)
     v = torch.tensor(synth.maxwell_boltzmann(s, 300.0, seed=7 + rank), dtype=torch.float32, device=dev)
@@ -364,14 +383,7 @@ def main_ours(args):
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     torch.cuda.set_device(local_rank)
     res = run_ours(args, rank, world, local_rank)
-    ms = res["total_ms"]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        te = torch.tensor([res["e2e_ms"]], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        res["e2e_ms"] = float(te.item())
+    ms, res["e2e_ms"] = max_over_ranks([res["total_ms"], res["e2e_ms"]], "cuda")
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()

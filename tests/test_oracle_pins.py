@@ -358,3 +358,17 @@ def test_vjp_against_central_differences(coulomb):
                 assert fd == pytest.approx(an, rel=1e-5, abs=1e-6 * max(1.0, abs(an)))
     # a single off-diagonal slot carries half of the symmetric derivative
     assert np.allclose(g["gc6"], g["gc6"].T)
+
+
+def test_energy_moments_are_squared_radial_derivatives():
+    # two atoms: m = (r dV/dr)^2 for each term, with dV/dr from central differences of the energy
+    for coulomb, beta, eps_rf in ((synth.COULOMB_RF, 0.0, math.inf), (synth.COULOMB_EWALD, 3.123413274340875, 1.0)):
+        r, h = 0.37, 1e-6
+        kw = dict(q=(0.7, -0.4), rc=1.0, coulomb=coulomb, beta=beta, eps_rf=eps_rf)
+        s = two_atoms(r, **kw)
+        m_lj, m_c = oracle.energy_moments(s)
+        op, om = oracle.brute(two_atoms(r + h, **kw)), oracle.brute(two_atoms(r - h, **kw))
+        d_lj = r * (op["E_lj"] - om["E_lj"]) / (2 * h)
+        d_c = r * (op["E_c"] - om["E_c"]) / (2 * h)
+        assert m_lj == pytest.approx(d_lj ** 2, rel=1e-6)
+        assert m_c == pytest.approx(d_c ** 2, rel=1e-6)
