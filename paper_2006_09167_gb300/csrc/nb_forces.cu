@@ -102,6 +102,7 @@ __global__ void k_gather(int nslots, const int *__restrict__ perm, const float *
 // constant here, the virial its factor -1/2).
 __global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__restrict__ fs, float *__restrict__ f,
                          const double *__restrict__ part, int n_part, double coul_f, double *e, double *vir) {
+    __shared__ double s_acc[256];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const float4 v = fs[inv[i]];
@@ -109,14 +110,25 @@ __global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__res
         f[3 * i + 1] = v.y;
         f[3 * i + 2] = v.z;
     }
-    if (part && threadIdx.x < 11) {
-        const int k = threadIdx.x;
-        if ((k < 2 && e) || (k >= 2 && vir)) {
-            double acc = 0.0;
-            for (int r = blockIdx.x; r < n_part; r += gridDim.x) acc += part[(size_t)r * 11 + k];
-            if (k == 0) atomicAdd(&e[0], acc);
-            else if (k == 1) atomicAdd(&e[1], coul_f * acc);
-            else atomicAdd(&vir[k - 2], -0.5 * acc);
+    if (!part) return;
+    // thread t folds value k = t % 11 of the rows r = blockIdx.x + G (t / 11 + 23 m)
+    const int k = threadIdx.x % 11, lane_row = threadIdx.x / 11;
+    double acc = 0.0;
+    if (threadIdx.x < 253) {
+        for (int r = blockIdx.x + gridDim.x * lane_row; r < n_part; r += gridDim.x * 23)
+            acc += part[(size_t)r * 11 + k];
+    }
+    s_acc[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < 11) {
+        double tot = 0.0;
+        for (int l = 0; l < 23; l++) tot += s_acc[l * 11 + threadIdx.x];
+        if (threadIdx.x == 0) {
+            if (e) atomicAdd(&e[0], tot);
+        } else if (threadIdx.x == 1) {
+            if (e) atomicAdd(&e[1], coul_f * tot);
+        } else if (vir) {
+            atomicAdd(&vir[threadIdx.x - 2], -0.5 * tot);
         }
     }
 }

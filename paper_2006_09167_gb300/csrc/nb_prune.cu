@@ -26,9 +26,14 @@ struct PruneArgs {
     int *inner_len;
 };
 
+// One warp per item; the warp works on 4 entries at a time (8 lanes each, lane
+// t of a group owning i-atom t of every i-cluster) so that four entries' loads
+// are in flight together -- the loop is latency-bound otherwise.  Surviving
+// entries are compacted in their original order.
 __global__ void __launch_bounds__(kPW * 32) k_prune(PruneArgs a) {
     __shared__ float4 s_xi[kPW][NB_SCA];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
     const long long w = (long long)blockIdx.x * kPW + wib;
     const long long item = a.part + w * a.n_parts;
     if (item >= a.n_items) return;
@@ -40,30 +45,39 @@ __global__ void __launch_bounds__(kPW * 32) k_prune(PruneArgs a) {
         s_xi[wib][at] = shift_i(a.xq[si * NB_SCA + at], sh);
     }
     __syncwarp();
-    const int ti = lane & 7, tj = lane >> 3;
+    const int g = lane >> 3, t = lane & 7;
     int cnt = 0;
-    for (int e = 0; e < len; e++) {
-        const int2 ent = a.cj_outer[j0 + e];
-        const int cj = ent.x, im = ent.y & 0xff;
-        const float4 xj0 = shift_j(a.xq[cj * NB_CL + tj], sh), xj1 = shift_j(a.xq[cj * NB_CL + tj + 4], sh);
+    for (int e0 = 0; e0 < len; e0 += 4) {
+        const int e = e0 + g;
+        const bool valid = e < len;
+        const int2 ent = valid ? a.cj_outer[j0 + e] : make_int2(0, 0);
+        const int im = ent.y & 0xff;
+        float4 xj[NB_CL];
+#pragma unroll
+        for (int b = 0; b < NB_CL; b++) xj[b] = shift_j(a.xq[ent.x * NB_CL + b], sh);
         int kept = 0;
 #pragma unroll
         for (int k = 0; k < NB_SCL; k++) {
             if (im & (1 << k)) {
-                const float4 xi = s_xi[wib][k * NB_CL + ti];
-                float dx = xi.x - xj0.x, dy = xi.y - xj0.y, dz = xi.z - xj0.z;
-                float r2a = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                dx = xi.x - xj1.x;
-                dy = xi.y - xj1.y;
-                dz = xi.z - xj1.z;
-                float r2b = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if (__any_sync(0xffffffffu, r2a < a.rin2 || r2b < a.rin2)) kept |= 1 << k;
+                const float4 xi = s_xi[wib][k * NB_CL + t];
+                bool any = false;
+#pragma unroll
+                for (int b = 0; b < NB_CL; b++) {
+                    const float dx = xi.x - xj[b].x, dy = xi.y - xj[b].y, dz = xi.z - xj[b].z;
+                    any |= fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < a.rin2;
+                }
+                kept |= (int)any << k;
             }
         }
-        if (kept) {
-            if (lane == 0) a.cj_inner[j0 + cnt] = make_int2(cj, (ent.y & ~0xff) | kept);
-            cnt++;
+        kept |= __shfl_xor_sync(full, kept, 1);
+        kept |= __shfl_xor_sync(full, kept, 2);
+        kept |= __shfl_xor_sync(full, kept, 4);
+        const unsigned keep = __ballot_sync(full, t == 0 && kept != 0);
+        if (t == 0 && kept != 0) {
+            const int pos = cnt + __popc(keep & ((1u << lane) - 1));
+            a.cj_inner[j0 + pos] = make_int2(ent.x, (ent.y & ~0xff) | kept);
         }
+        cnt += __popc(keep);
     }
     if (lane == 0) a.inner_len[item] = cnt;
 }
