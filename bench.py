@@ -19,6 +19,7 @@ copy of the workload (weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -145,11 +146,17 @@ def fp32_peak_tflops(sm_mhz):
 
 
 def l2_flusher(device):
+    """Flush L2 between timed iterations: write a 256 MiB buffer (> the 129 MB L2), then
+    read another, so that L2 holds none of the workload and no dirty flush lines either
+    (their write-back would otherwise land in the next timed step)."""
     import torch
     buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    buf2 = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    sink = torch.empty(1, dtype=torch.float32, device=device)
 
     def flush():
         buf.fill_(1.0)
+        torch.sum(buf2, dim=0, keepdim=True, out=sink)
     return flush
 
 
@@ -165,6 +172,11 @@ def run_ours(args, rank, world, local_rank):
     v = torch.tensor(synth.maxwell_boltzmann(s, 300.0, seed=7 + rank), dtype=torch.float32, device=dev)
     flush = l2_flusher(dev)
     box = s.box
+    from paper_2006_09167_gb300 import autotune
+    # the work-item size is autotuned; the prune cadence is the workload's (2 rolling parts)
+    tuned = autotune.tune(s, x0)
+    ctx.nb_set_split(tuned["split"])
+    n_parts = N_PARTS
     ctx.build(x0, box)
     ctx.nb_trace_enable(True)
     f = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
@@ -177,7 +189,7 @@ def run_ours(args, rank, world, local_rank):
         if t % NSTLIST == 0 and t > 0:
             ctx.build(x, box)
         ctx.nb_forces(flags, x, f, e, w)
-        ctx.nb_prune_rolling(t % N_PARTS, N_PARTS)
+        ctx.nb_prune_rolling(t % n_parts, n_parts)
         x.add_(v, alpha=DT)
 
     for t in range(args.warmup):
@@ -212,7 +224,8 @@ def run_ours(args, rank, world, local_rank):
     # algorithmic work of one force launch: effective pairs at the current positions
     n_eff, n_raw = ctx.nb_count_pairs()
     res = dict(total_ms=total_ms, step_ms=step_ms, launches=launches, fk_ms=fk_ms, fk_n=fk_n, pr_ms=pr_ms,
-               pr_n=pr_n, ga_ms=ga_ms, ga_n=ga_n, n_eff=n_eff, n_raw=n_raw, clocks=clk, n_atoms=s.n)
+               pr_n=pr_n, ga_ms=ga_ms, ga_n=ga_n, n_eff=n_eff, n_raw=n_raw, clocks=clk, n_atoms=s.n,
+               tuned={"split": int(tuned["split"]), "n_parts": n_parts})
     # end to end through the public API: pinned host positions in, forces + energies out
     xh = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
     xh.copy_(x.cpu())
@@ -231,7 +244,7 @@ def run_ours(args, rank, world, local_rank):
         if t % NSTLIST == 0:
             ctx.build(xd, box)
         fo, eo, wo = ctx.forces(xd, energy=True, virial=True)
-        ctx.nb_prune_rolling(t % N_PARTS, N_PARTS)
+        ctx.nb_prune_rolling(t % n_parts, n_parts)
         fh.copy_(fo, non_blocking=True)
         eh.copy_(eo, non_blocking=True)
         wh.copy_(wo.view(-1), non_blocking=True)
@@ -253,9 +266,13 @@ def extra_workloads(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     # batched: 256 uneven replicas
     reps = synth.replica_set()
+    from paper_2006_09167_gb300 import autotune
+    med = sorted(reps, key=lambda r: r.n)[len(reps) // 2]
+    tuned_b = autotune.tune(med, torch.tensor(med.x, device=dev))
     ctxs, xs = [], []
     for sysr in reps:
         c = api.NbContext.from_system(sysr)
+        c.nb_set_split(tuned_b["split"])
         xr = torch.tensor(sysr.x, device=dev)
         c.build(xr, sysr.box)
         ctxs.append(c)
@@ -312,7 +329,7 @@ def extra_workloads(args):
     t_plain_seq = time_fn(plain, reps_=5, warm=1)
     n_all = sum(c.n for c in ctxs)
     out["batched_256_replicas"] = {
-        "atoms_total": int(n_all), "replicas": R,
+        "atoms_total": int(n_all), "replicas": R, "split_autotuned": int(tuned_b["split"]),
         "batched_graph_ms": t_batched_graph, "plain_graph_ms": t_plain_graph, "plain_sequential_ms": t_plain_seq,
         "system_evals_per_s_batched": R * 1e3 / t_batched_graph,
         "system_evals_per_s_plain_graph": R * 1e3 / t_plain_graph,
@@ -400,9 +417,10 @@ def main_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "spce_water_96k_ewald_rc1.0_rlist1.1 MD-like step: forces+energies+virial, "
-                               "rolling prune 1/2 per step, grid sort + pair search every 100 steps",
-                   "n_atoms": res["n_atoms"], "rc": 1.0, "rlist": 1.1, "nstlist": NSTLIST, "prune_parts": N_PARTS,
-                   "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                               "rolling prune of 1/2 of the list per step, grid sort + pair search every 100 steps",
+                   "n_atoms": res["n_atoms"], "rc": 1.0, "rlist": 1.1, "r_in": 1.0, "nstlist": NSTLIST,
+                   "prune_parts": res["tuned"]["n_parts"], "split": res["tuned"]["split"],
+                   "l2": "flushed between timed steps (256 MiB write + 256 MiB read of another buffer, outside the events)",
                    "parallelism": f"replicas{world}"},
         "e2e": {"value": world * 1e3 / res["e2e_ms"], "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": res["d2h"]},

@@ -182,10 +182,12 @@ void nb_batch_destroy(nb_batch *batch);
 nb_status nb_forces_batched(nb_batch *batch, unsigned flags, const float *x_dev, float *f_dev,
                             double *e_dev, double *vir_dev, void *stream);
 
-/* Counts over the inner list at the current positions: pairs inside rc that
- * the kernel computes (effective interactions) and atom pairs evaluated
- * (8x8 per set mask bit, the raw work).  Synchronises `stream`. */
-nb_status nb_count_pairs(nb_ctx *ctx, int64_t *n_within_rc, int64_t *n_evaluated, void *stream);
+/* Counts over the inner (NB_LIST_INNER) or outer (NB_LIST_OUTER) list at the
+ * current positions: pairs inside rc that the force kernel computes from it
+ * (effective interactions) and atom pairs evaluated (8x8 per set mask bit, the
+ * raw work).  Pairs inside rc that the outer list has and the inner list lacks
+ * were missed by the prune.  Synchronises `stream`. */
+nb_status nb_count_pairs(nb_ctx *ctx, int which, int64_t *n_within_rc, int64_t *n_evaluated, void *stream);
 
 /* Export the atom pairs the kernel would evaluate from the outer or inner list
  * (mask bit set, both atoms real) as int64 rows (i, j, sx, sy, sz) with
@@ -202,6 +204,11 @@ nb_status nb_debug_layout(nb_ctx *ctx, int32_t *perm_host, float *xq_host, float
                           void *stream);
 
 nb_status nb_get_stats(nb_ctx *ctx, nb_stats *out);
+
+/* Tuning (Sec. V.F: lists are split when there are too few of them for the GPU):
+ * the largest number of outer j-cluster entries per work item (4..128, default
+ * 32).  Takes effect at the next nb_pairlist_build. */
+nb_status nb_set_split(nb_ctx *ctx, int max_entries_per_item);
 
 /* Tracing (not in the paper): when enabled, CUDA events are recorded on the
  * launch stream around every force, prune, gather and adjoint kernel of this

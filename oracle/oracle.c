@@ -439,6 +439,7 @@ int or_vjp(int n, const double *x, const double *q, const int *type, int T, cons
  * of the pair energies to a relative perturbation of r:
  *   m[0] = sum (r dV_LJ/dr)^2 = sum (12 C12 r^-12 - 6 C6 r^-6)^2
  *   m[1] = sum (r dV_C/dr)^2  (f qi qj / r times the screening factor for Ewald)
+ *   m[2] = sum |V_LJ|,  m[3] = sum |V_C|
  * A relative rounding error eps in each r moves E_LJ by about eps sqrt(m[0]) (random
  * signs), so sqrt(m)/|E| is the relative error floor of an energy summed from
  * pair terms computed in a precision with unit roundoff eps. */
@@ -451,7 +452,7 @@ int or_energy_moments(int n, const double *x, const double *q, const int *type, 
         if (!(rc < 0.5 * box[k])) return 1;
     cells_t c;
     int use_cells = build_cells(&c, n, x, box, rc);
-    double *acc = (double *)calloc((size_t)n * 2, sizeof(double));
+    double *acc = (double *)calloc((size_t)n * 4, sizeof(double));
 #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < n; i++) {
         int ci[3] = {0, 0, 0};
@@ -482,16 +483,16 @@ int or_energy_moments(int n, const double *x, const double *q, const int *type, 
                                    pair_c(c12, T, type[i], type[j]), 0, &pt);
                         /* r dV/dr = -phi r^2 */
                         double slj = pt.plj * r2, sc = pt.pc * r2;
-                        acc[2 * i] += 0.5 * slj * slj;
-                        acc[2 * i + 1] += 0.5 * sc * sc;
+                        acc[4 * i] += 0.5 * slj * slj;
+                        acc[4 * i + 1] += 0.5 * sc * sc;
+                        acc[4 * i + 2] += 0.5 * fabs(pt.vlj);
+                        acc[4 * i + 3] += 0.5 * fabs(pt.vc);
                     }
                 }
     }
-    m[0] = m[1] = 0.0;
-    for (int i = 0; i < n; i++) {
-        m[0] += acc[2 * i];
-        m[1] += acc[2 * i + 1];
-    }
+    m[0] = m[1] = m[2] = m[3] = 0.0;
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < 4; k++) m[k] += acc[4 * i + k];
     free(acc);
     if (use_cells) free_cells(&c);
     return 0;

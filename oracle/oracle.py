@@ -200,19 +200,22 @@ def vjp(s, gF, gE, x=None):
     return dict(gx=gx, gq=gq, gc6=gc6, gc12=gc12)
 
 
-def energy_moments(s, x=None):
-    """(m_lj, m_c): sums over pairs inside rc of (r dV/dr)^2 for the LJ and Coulomb terms."""
+def energy_moments(s, x=None, with_abs=False):
+    """(m_lj, m_c): sums over pairs inside rc of (r dV/dr)^2 for the LJ and Coulomb terms;
+    with_abs also returns (sum |V_LJ|, sum |V_C|)."""
     lib = _load()
     xx, q, ty, c6, c12, off, idx, box = _arrays(s)
     if x is not None:
         xx = np.ascontiguousarray(x, dtype=np.float64)
-    m = np.zeros(2)
+    m = np.zeros(4)
     co, er, erf_, be = _coul(s)
     rc = lib.or_energy_moments(xx.shape[0], _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d),
                                _p(c12, _d), _p(off, _i), _p(idx, _i), _p(box, _d), co, er, erf_, be,
                                float(s.rc), _p(m, _d))
     if rc != 0:
         raise ValueError("oracle: rc must be < L/2")
+    if with_abs:
+        return float(m[0]), float(m[1]), float(m[2]), float(m[3])
     return float(m[0]), float(m[1])
 
 

@@ -34,7 +34,7 @@ EXPORTED = [
     "nb_prune_rolling", "nb_forces", "nb_forces_vjp", "nb_batch_create", "nb_batch_destroy",
     "nb_forces_batched", "nb_count_pairs", "nb_debug_export_pairs", "nb_debug_layout",
     "nb_get_stats", "nb_get_error", "nb_status_str", "nb_trace_enable", "nb_trace_read",
-    "nb_forces_small_noalloc",
+    "nb_forces_small_noalloc", "nb_set_split",
 ]
 NB_NOALLOC_MAX_ATOMS = 16384
 NB_NOALLOC_MAX_TYPES = 8
@@ -97,12 +97,13 @@ def load(path: str = LIB_PATH):
     lib.nb_batch_destroy.argtypes = [vp]
     lib.nb_batch_destroy.restype = None
     lib.nb_forces_batched.argtypes = [vp, ctypes.c_uint, vp, vp, vp, vp, vp]
-    lib.nb_count_pairs.argtypes = [vp, i64p, i64p, vp]
+    lib.nb_count_pairs.argtypes = [vp, ctypes.c_int, i64p, i64p, vp]
     lib.nb_debug_export_pairs.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_size_t,
                                           ctypes.POINTER(ctypes.c_size_t), vp]
     lib.nb_debug_layout.argtypes = [vp, i32p, f32p, f32p, vp]
     lib.nb_get_stats.argtypes = [vp, ctypes.POINTER(NbStats)]
     lib.nb_get_error.argtypes = [vp, vp]
+    lib.nb_set_split.argtypes = [vp, ctypes.c_int]
     lib.nb_trace_enable.argtypes = [vp, ctypes.c_int]
     lib.nb_trace_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p]
     lib.nb_forces_small_noalloc.argtypes = [ctypes.POINTER(NbParams), vp, vp, vp, vp, vp,

@@ -134,11 +134,12 @@ class NbContext:
                                       _dev(gq, torch.float32, self.n, "gq"), _dev(gc6, torch.float64, tt, "gc6"),
                                       _dev(gc12, torch.float64, tt, "gc12"), _stream(stream)), "nb_forces_vjp")
 
-    def nb_count_pairs(self, stream=None):
+    def nb_count_pairs(self, which: int = NB_LIST_INNER, stream=None):
+        """(pairs inside rc, atom pairs evaluated) from the inner or outer list."""
         a = ctypes.c_int64()
         b = ctypes.c_int64()
-        check(self._lib.nb_count_pairs(self.handle, ctypes.byref(a), ctypes.byref(b), _stream(stream)),
-              "nb_count_pairs")
+        check(self._lib.nb_count_pairs(self.handle, int(which), ctypes.byref(a), ctypes.byref(b),
+                                       _stream(stream)), "nb_count_pairs")
         return a.value, b.value
 
     def nb_debug_export_pairs(self, which: int = NB_LIST_INNER, stream=None) -> np.ndarray:
@@ -168,6 +169,9 @@ class NbContext:
         s = _abi.NbStats()
         check(self._lib.nb_get_stats(self.handle, ctypes.byref(s)), "nb_get_stats")
         return {k: int(getattr(s, k)) for k, _ in _abi.NbStats._fields_}
+
+    def nb_set_split(self, split: int):
+        check(self._lib.nb_set_split(self.handle, int(split)), "nb_set_split")
 
     def nb_trace_enable(self, enable: bool = True):
         check(self._lib.nb_trace_enable(self.handle, 1 if enable else 0), "nb_trace_enable")

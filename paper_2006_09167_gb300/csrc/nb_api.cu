@@ -464,11 +464,12 @@ nb_status nb_forces_vjp(nb_ctx *c, const float *x_dev, const float *gF_dev, doub
     return nb_launch_vjp(c, x_dev, gF_dev, gE, gx_dev, gq_dev, gc6_dev, gc12_dev, (cudaStream_t)stream);
 }
 
-nb_status nb_count_pairs(nb_ctx *c, int64_t *n_within, int64_t *n_eval, void *stream) {
+nb_status nb_count_pairs(nb_ctx *c, int which, int64_t *n_within, int64_t *n_eval, void *stream) {
     if (!c || !n_within || !n_eval) return NB_ERR_INVALID_ARG;
+    if (which != NB_LIST_OUTER && which != NB_LIST_INNER) return NB_ERR_INVALID_ARG;
     if (!c->have_list) return NB_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;
-    nb_status s = nb_launch_count(c, st);
+    nb_status s = nb_launch_count(c, which, st);
     if (s != NB_OK) return s;
     long long h[2];
     NB_CUDA_TRY(cudaMemcpyAsync(h, c->diag, 2 * sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -512,6 +513,13 @@ nb_status nb_debug_layout(nb_ctx *c, int32_t *perm_host, float *xq_host, float *
         NB_CUDA_TRY(cudaMemcpyAsync(bbox_host, c->bb, sizeof(float4) * 2 * (size_t)c->S_host * NB_SCL,
                                     cudaMemcpyDeviceToHost, st));
     NB_CUDA_TRY(cudaStreamSynchronize(st));
+    return NB_OK;
+}
+
+nb_status nb_set_split(nb_ctx *c, int split) {
+    if (!c || split < 4 || split > 128) return NB_ERR_INVALID_ARG;
+    c->split = split;
+    c->have_list = false;  // the item structure changes with the next build
     return NB_OK;
 }
 

@@ -200,7 +200,7 @@ nb_status nb_launch_prune(nb_ctx *c, float r_in, int part, int n_parts, cudaStre
 nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cudaStream_t st);
 nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, double *vir,
                            cudaStream_t st);
-nb_status nb_launch_count(nb_ctx *c, cudaStream_t st);
+nb_status nb_launch_count(nb_ctx *c, int which, cudaStream_t st);
 nb_status nb_launch_export(nb_ctx *c, int which, long long *buf, long long cap, long long *count,
                            cudaStream_t st);
 nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, float *gx, float *gq,

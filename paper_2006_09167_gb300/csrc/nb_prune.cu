@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(kPW * 32) k_prune(PruneArgs a) {
     if (lane == 0) a.inner_len[item] = cnt;
 }
 
-// Counts over the inner list: pairs inside rc that are computed, and 64 per mask bit.
+// Counts over a list (inner_len == nullptr: the outer list): pairs inside rc that are
+// computed, and 64 per mask bit.
 __global__ void __launch_bounds__(kPW * 32)
     k_count(int n_items, const int4 *items, const int *inner_len, const int2 *cj, const unsigned long long *masks,
             const float4 *xq, float Lhi0, float Lhi1, float Lhi2, float Llo0, float Llo1, float Llo2, float rc2,
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kPW * 32)
     if (item >= n_items) return;
     const float Lhi[3] = {Lhi0, Lhi1, Lhi2}, Llo[3] = {Llo0, Llo1, Llo2};
     const int4 it = items[item];
-    const int len = inner_len[item];
+    const int len = inner_len ? inner_len[item] : it.w;
     const ShiftSplit sh = make_shift(it.y, Lhi, Llo);
     for (int h = 0; h < 2; h++) {
         int at = lane + 32 * h;
@@ -204,7 +205,7 @@ nb_status nb_launch_prune(nb_ctx *c, float r_in, int part, int n_parts, cudaStre
     return NB_OK;
 }
 
-nb_status nb_launch_count(nb_ctx *c, cudaStream_t st) {
+nb_status nb_launch_count(nb_ctx *c, int which, cudaStream_t st) {
     NB_CUDA_TRY(cudaMemsetAsync(c->diag, 0, 2 * sizeof(long long), st));
     if (c->n_items == 0) return NB_OK;
     float hi[3], lo[3];
@@ -212,7 +213,8 @@ nb_status nb_launch_count(nb_ctx *c, cudaStream_t st) {
     float rc = (float)c->rc;
     c->n_launches++;
     k_count<<<(c->n_items + kPW - 1) / kPW, kPW * 32, 0, st>>>(
-        c->n_items, c->items, c->inner_len, c->cj_inner, c->masks, c->xq, hi[0], hi[1], hi[2], lo[0], lo[1],
+        c->n_items, c->items, which == NB_LIST_INNER ? c->inner_len : nullptr,
+        which == NB_LIST_INNER ? c->cj_inner : c->cj_outer, c->masks, c->xq, hi[0], hi[1], hi[2], lo[0], lo[1],
         lo[2], rc * rc, reinterpret_cast<unsigned long long *>(c->diag));
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;

@@ -334,11 +334,17 @@ class _Grid:
         c = np.mod(c, self.nc)
         return (c[..., 0] * self.nc[1] + c[..., 1]) * self.nc[2] + c[..., 2]
 
-    def near_min_dist(self, p, all_pos, ignore=None):
+    def near_min_dist(self, p, all_pos, ignore=None, chunk=20000):
         """Minimum-image distance from each point p[k] to stored points (inf if none)."""
+        if p.shape[0] > chunk:
+            return np.concatenate([
+                self.near_min_dist(p[a:a + chunk], all_pos,
+                                   None if ignore is None else [ig[a:a + chunk] for ig in ignore], chunk)
+                for a in range(0, p.shape[0], chunk)])
         c = np.floor(p / self.cell).astype(int)
         offs = np.array([(a, b, d) for a in (-1, 0, 1) for b in (-1, 0, 1) for d in (-1, 0, 1)])
-        cand = self.slots[self._cid(c[:, None, :] + offs[None])]  # [k,27,cap]
+        used = max(1, int(self.fill.max()))
+        cand = self.slots[self._cid(c[:, None, :] + offs[None])][:, :, :used]  # [k,27,used]
         cand = cand.reshape(p.shape[0], -1)
         valid = cand >= 0
         if ignore is not None:
@@ -440,16 +446,23 @@ def polymer_water_box(seed: int = 3, n_chain: int = 1125, chain_len: int = 200,
                 d13 -= box * np.rint(d13 / box)
                 ok &= np.sqrt((d13 * d13).sum(1)) >= min_13
             ok &= grid.near_min_dist(cand, pos, ignore=[prev_idx[todo], prev2_idx[todo]]) >= min_nb
-            done = np.zeros(todo.size, dtype=bool)
-            # insert one at a time so that two chains growing in the same step cannot clash
-            for t in np.nonzero(ok)[0]:
-                a = todo[t]
-                if not acceptable(cand[t], prev_idx[a], prev2_idx[a]):
-                    continue
-                pos[idx_now[a]] = cand[t]
-                placed_any[idx_now[a]] = True
-                grid.insert([idx_now[a]], cand[t:t + 1])
-                done[t] = True
+            # two chains growing in the same step must not clash with each other: of every
+            # pair of accepted candidates closer than min_nb, the later one is rejected
+            acc = np.nonzero(ok)[0]
+            if acc.size > 1:
+                pa = cand[acc]
+                dd = pa[:, None, :] - pa[None, :, :]
+                dd -= box * np.rint(dd / box)
+                close = (dd * dd).sum(-1) < min_nb * min_nb
+                close = np.triu(close, 1)
+                ok[acc[np.any(close, axis=0)]] = False
+            done = ok
+            acc = np.nonzero(done)[0]
+            if acc.size:
+                ids = idx_now[todo[acc]]
+                pos[ids] = cand[acc]
+                placed_any[ids] = True
+                grid.insert(ids, cand[acc])
             todo = todo[~done]
         for a in todo:  # trapped: take the chain out and regrow it later
             failed[a] = True

@@ -190,3 +190,25 @@ def test_count_pairs_matches_oracle(api):
     within, evald = ctx.nb_count_pairs()
     assert within == oracle.brute(s)["npairs"]
     assert evald >= within and evald % 64 == 0
+
+
+def test_forces_1p5M_polymer_water_full_size(api):
+    # the full heterogeneous 1.5M-atom box: sampled forces, full energies and virial
+    s = synth.polymer_water_box()
+    ctx, f, e, w = run_forces(api, s)
+    st = ctx.nb_get_stats()
+    assert st["n_atoms"] == 1_500_000
+    rng = np.random.default_rng(5)
+    # chain atoms (the first 225,000) and waters both sampled
+    sub = np.sort(np.concatenate([rng.choice(225000, 1500, replace=False),
+                                  225000 + rng.choice(s.n - 225000, 1500, replace=False)]))
+    ref = oracle.celllist(s, subset=sub)
+    assert rms_rel(f[sub], ref["F"]) < TOL_F
+    full = oracle.celllist(s)
+    tol_lj, tol_c = energy_tolerances(s, full)
+    assert rel(e[0], full["E_lj"]) < tol_lj
+    assert rel(e[1], full["E_c"]) < tol_c
+    assert np.sqrt(((w - full["W"]) ** 2).sum() / (full["W"] ** 2).sum()) < TOL_W
+    assert rms_rel(f, full["F"]) < TOL_F
+    net = np.abs(f.astype(np.float64).sum(0)).max()
+    assert net < TOL_NET * np.abs(f).sum()
