@@ -361,6 +361,23 @@ def extra_workloads(args):
     t_fa = time_fn(graphed(fwd_adj).replay)
     out["fwd_adjoint_24k"] = {"n_atoms": s4.n, "forward_ms": t_f, "forward_adjoint_ms": t_fa,
                               "evals_per_s_forward": 1e3 / t_f, "evals_per_s_forward_adjoint": 1e3 / t_fa}
+    # LJ argon throughput against the number of pairs per particle (the paper's Fig. 6
+    # system: 157k atoms, rho 26 nm^-3, sigma 0.3345 nm; force-only, LJ-only kernel)
+    sweep = []
+    for rc in (0.5, 0.7, 0.9, 1.1, 1.4, 1.8):
+        sa = synth.argon_box(157000, seed=11, rc=rc, rlist=rc + 0.1)
+        ca = api.NbContext.from_system(sa)
+        xa = torch.tensor(sa.x, device=dev)
+        ca.build(xa, sa.box)
+        fa = torch.empty_like(xa)
+        ta = time_fn(lambda: ca.nb_forces(0, xa, fa), reps_=10)
+        n_eff, n_raw = ca.nb_count_pairs()
+        sweep.append({"rc": rc, "pairs_per_particle_half_sphere": 2.0 * math.pi / 3.0 * 26.0 * rc ** 3,
+                      "force_ms": ta, "raw_Gpairs_per_s": n_raw / (ta * 1e-3) / 1e9,
+                      "effective_Gpairs_per_s": n_eff / (ta * 1e-3) / 1e9,
+                      "work_efficiency": n_eff / max(n_raw, 1)})
+        del ca
+    out["argon_157k_sweep"] = sweep
     if args.full:
         s3 = synth.polymer_water_box()
         c3 = api.NbContext.from_system(s3)

@@ -64,7 +64,7 @@ typedef enum {
     NB_ERR_NONFINITE = 7      /* non-finite coordinates were seen on the device */
 } nb_status;
 
-enum { NB_COULOMB_RF = 0, NB_COULOMB_EWALD = 1 };
+enum { NB_COULOMB_RF = 0, NB_COULOMB_EWALD = 1, NB_COULOMB_NONE = 2 /* Lennard-Jones only */ };
 
 /* flags of nb_forces / nb_forces_batched */
 enum { NB_ENERGY = 1u, NB_VIRIAL = 2u };
@@ -75,7 +75,7 @@ enum { NB_LIST_OUTER = 0, NB_LIST_INNER = 1 };
 typedef struct {
     int32_t n_atoms;  /* N >= 1 */
     int32_t n_types;  /* T in [1, 64] */
-    int32_t coulomb;  /* NB_COULOMB_RF or NB_COULOMB_EWALD */
+    int32_t coulomb;  /* NB_COULOMB_RF, NB_COULOMB_EWALD or NB_COULOMB_NONE */
     int32_t reserved; /* must be 0 */
     double eps_r;     /* relative permittivity (> 0) */
     double eps_rf;    /* reaction-field dielectric; +inf (or <= 0) = conducting */

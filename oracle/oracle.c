@@ -42,6 +42,7 @@
 
 #define OR_COULOMB_RF 0
 #define OR_COULOMB_EWALD 1
+#define OR_COULOMB_NONE 2 /* Lennard-Jones only */
 
 typedef struct {
     int coulomb;
@@ -89,7 +90,9 @@ static void pair_terms(const setup_t *s, double r2, double qq, double c6, double
     o->vlj = c12 * ir12 - c6 * ir6 - (c12 * rc12 - c6 * rc6);
     o->plj = (12.0 * c12 * ir12 - 6.0 * c6 * ir6) * ir2;
     double vcu, pcu, dpcu;
-    if (s->coulomb == OR_COULOMB_RF) {
+    if (s->coulomb == OR_COULOMB_NONE) {
+        vcu = pcu = dpcu = 0.0;
+    } else if (s->coulomb == OR_COULOMB_RF) {
         vcu = s->f * (ir + s->k_rf * r2 - s->c_rf);
         pcu = s->f * (ir * ir2 - 2.0 * s->k_rf);
         dpcu = s->f * (-3.0 * ir2 * ir2);

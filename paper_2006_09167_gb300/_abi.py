@@ -23,6 +23,7 @@ NB_ERR_NONFINITE = 7
 
 NB_COULOMB_RF = 0
 NB_COULOMB_EWALD = 1
+NB_COULOMB_NONE = 2
 NB_ENERGY = 1
 NB_VIRIAL = 2
 NB_LIST_OUTER = 0

@@ -15,7 +15,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (NB_COULOMB_EWALD, NB_COULOMB_RF, NB_ENERGY, NB_LIST_INNER, NB_LIST_OUTER,  # noqa: F401
+from ._abi import (NB_COULOMB_EWALD, NB_COULOMB_NONE, NB_COULOMB_RF, NB_ENERGY, NB_LIST_INNER, NB_LIST_OUTER,  # noqa: F401
                    NB_TRACE_FORCES, NB_TRACE_GATHER, NB_TRACE_PRUNE, NB_TRACE_VJP, NB_VIRIAL, NbError, check)
 
 

@@ -141,7 +141,8 @@ nb_status nb_create(const nb_params *p, const float *q_host, const int32_t *type
     if (!p || !q_host || !type_host || !p->c6_host || !p->c12_host) return NB_ERR_INVALID_ARG;
     const int N = p->n_atoms, T = p->n_types;
     if (N < 1 || T < 1 || T > NB_MAX_TYPES || p->reserved != 0) return NB_ERR_INVALID_ARG;
-    if (p->coulomb != NB_COULOMB_RF && p->coulomb != NB_COULOMB_EWALD) return NB_ERR_INVALID_ARG;
+    if (p->coulomb != NB_COULOMB_RF && p->coulomb != NB_COULOMB_EWALD && p->coulomb != NB_COULOMB_NONE)
+        return NB_ERR_INVALID_ARG;
     if (!finite_pos(p->eps_r) || !finite_pos(p->rc) || !finite_pos(p->rlist) || !finite_pos(p->r_in))
         return NB_ERR_INVALID_ARG;
     if (p->rc > 8.0 || p->r_in < p->rc || p->rlist < p->r_in) return NB_ERR_INVALID_ARG;

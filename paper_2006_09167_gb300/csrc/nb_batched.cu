@@ -226,8 +226,9 @@ nb_status nb_batch_create(nb_ctx *const *ctxs, int n, nb_batch **out) {
         nb_batch_destroy(b);
         return nb_cuda_status(err);
     }
-    int occ = b->coulomb == NB_COULOMB_RF ? occupancy<NB_COULOMB_RF, true, true>()
-                                          : occupancy<NB_COULOMB_EWALD, true, true>();
+    int occ = b->coulomb == NB_COULOMB_RF      ? occupancy<NB_COULOMB_RF, true, true>()
+              : b->coulomb == NB_COULOMB_EWALD ? occupancy<NB_COULOMB_EWALD, true, true>()
+                                               : occupancy<NB_COULOMB_NONE, true, true>();
     b->grid = std::max(1, std::min(sms * occ, (b->total_items + kBW - 1) / kBW));
     *out = b;
     return NB_OK;
@@ -253,11 +254,16 @@ nb_status nb_forces_batched(nb_batch *b, unsigned flags, const float *x, float *
             else if (en) NB_BATCH_LAUNCH(NB_COULOMB_RF, true, false);
             else if (vi) NB_BATCH_LAUNCH(NB_COULOMB_RF, false, true);
             else NB_BATCH_LAUNCH(NB_COULOMB_RF, false, false);
-        } else {
+        } else if (b->coulomb == NB_COULOMB_EWALD) {
             if (en && vi) NB_BATCH_LAUNCH(NB_COULOMB_EWALD, true, true);
             else if (en) NB_BATCH_LAUNCH(NB_COULOMB_EWALD, true, false);
             else if (vi) NB_BATCH_LAUNCH(NB_COULOMB_EWALD, false, true);
             else NB_BATCH_LAUNCH(NB_COULOMB_EWALD, false, false);
+        } else {
+            if (en && vi) NB_BATCH_LAUNCH(NB_COULOMB_NONE, true, true);
+            else if (en) NB_BATCH_LAUNCH(NB_COULOMB_NONE, true, false);
+            else if (vi) NB_BATCH_LAUNCH(NB_COULOMB_NONE, false, true);
+            else NB_BATCH_LAUNCH(NB_COULOMB_NONE, false, false);
         }
 #undef NB_BATCH_LAUNCH
     }

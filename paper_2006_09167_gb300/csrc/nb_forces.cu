@@ -158,11 +158,16 @@ void nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, cudaStrea
         else if (en) launch_forces_t<NB_COULOMB_RF, true, false>(v, st);
         else if (vi) launch_forces_t<NB_COULOMB_RF, false, true>(v, st);
         else launch_forces_t<NB_COULOMB_RF, false, false>(v, st);
-    } else {
+    } else if (coulomb == NB_COULOMB_EWALD) {
         if (en && vi) launch_forces_t<NB_COULOMB_EWALD, true, true>(v, st);
         else if (en) launch_forces_t<NB_COULOMB_EWALD, true, false>(v, st);
         else if (vi) launch_forces_t<NB_COULOMB_EWALD, false, true>(v, st);
         else launch_forces_t<NB_COULOMB_EWALD, false, false>(v, st);
+    } else {
+        if (en && vi) launch_forces_t<NB_COULOMB_NONE, true, true>(v, st);
+        else if (en) launch_forces_t<NB_COULOMB_NONE, true, false>(v, st);
+        else if (vi) launch_forces_t<NB_COULOMB_NONE, false, true>(v, st);
+        else launch_forces_t<NB_COULOMB_NONE, false, false>(v, st);
     }
 }
 

@@ -201,7 +201,8 @@ extern "C" nb_status nb_forces_small_noalloc(const nb_params *p, const float *x_
     const int n = p->n_atoms, T = p->n_types;
     if (n < 1 || T < 1 || p->reserved != 0) return NB_ERR_INVALID_ARG;
     if (n > NB_NOALLOC_MAX_ATOMS || T > NB_NOALLOC_MAX_TYPES) return NB_ERR_CAPACITY;
-    if (p->coulomb != NB_COULOMB_RF && p->coulomb != NB_COULOMB_EWALD) return NB_ERR_INVALID_ARG;
+    if (p->coulomb != NB_COULOMB_RF && p->coulomb != NB_COULOMB_EWALD && p->coulomb != NB_COULOMB_NONE)
+        return NB_ERR_INVALID_ARG;
     if (!pos_finite(p->eps_r) || !pos_finite(p->rc) || isnan(p->eps_rf)) return NB_ERR_INVALID_ARG;
     if (p->coulomb == NB_COULOMB_EWALD && (!pos_finite(p->beta) || p->beta * p->rc > NB_EW_ZMAX_D))
         return NB_ERR_INVALID_ARG;
@@ -280,9 +281,12 @@ extern "C" nb_status nb_forces_small_noalloc(const nb_params *p, const float *x_
     if (p->coulomb == NB_COULOMB_RF) {
         if (en) k_na_forces<NB_COULOMB_RF, true><<<grid, kNaThreads, 0, st>>>(a);
         else k_na_forces<NB_COULOMB_RF, false><<<grid, kNaThreads, 0, st>>>(a);
-    } else {
+    } else if (p->coulomb == NB_COULOMB_EWALD) {
         if (en) k_na_forces<NB_COULOMB_EWALD, true><<<grid, kNaThreads, 0, st>>>(a);
         else k_na_forces<NB_COULOMB_EWALD, false><<<grid, kNaThreads, 0, st>>>(a);
+    } else {
+        if (en) k_na_forces<NB_COULOMB_NONE, true><<<grid, kNaThreads, 0, st>>>(a);
+        else k_na_forces<NB_COULOMB_NONE, false><<<grid, kNaThreads, 0, st>>>(a);
     }
     if (en) k_na_finish<<<1, 32, 0, st>>>(a, (int)(grid.x * grid.y));
     NB_CUDA_TRY(cudaGetLastError());

@@ -134,10 +134,10 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
     const float2 lj = ljt[tpair];  // (6 C6, 12 C12)
     const float flj = rinv6 * fmaf(lj.y, rinv6, -lj.x);
     const float qq = qi * qj;
-    float fc;
+    float fc = 0.f;
     if (COUL == NB_COULOMB_RF) {
         fc = qq * fmaf(rinv, rinv2, -2.0f * v.k_rf);
-    } else {
+    } else if (COUL == NB_COULOMB_EWALD) {
         fc = qq * fmaf(rinv, rinv2, -v.ew_beta3 * ew_h(r2 * v.ew_s));
     }
     if (EN) fc *= v.coul_f;
@@ -146,7 +146,7 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
     if (EN) {
         const float4 le = lje[tpair];  // (C6, C12, C12/rc^12 - C6/rc^6, -)
         const float vlj = fmaf(rinv6, fmaf(le.y, rinv6, -le.x), -le.z);
-        float vc;
+        float vc = 0.f;
         if (COUL == NB_COULOMB_RF) {
             // 1/r as a float pair (rinv + rlo) from the exact residual 1 - r2 rinv^2;
             // (rinv - c_rf) is then exact near the cut-off, where the terms cancel
@@ -155,7 +155,7 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
             const float e = fmaf(-r2, t_hi, 1.0f) - r2 * t_lo;
             const float rlo = 0.5f * rinv * e;
             vc = (rinv - v.c_rf) + (fmaf(v.k_rf, r2, -v.c_rf_lo) + rlo);
-        } else {
+        } else if (COUL == NB_COULOMB_EWALD) {
             // CUDA's erfcf: measured against FP64 erfc it has the smallest bias of the
             // variants tried (the energy totals of water sum 10^5-10^7 cancelling terms)
             vc = fmaf(erfcf(v.ew_beta * (r2 * rinv)), rinv, -v.ew_shift);

@@ -107,12 +107,12 @@ __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v) {
                 const float phi_lj = fmaf(12.f * le.y, rinv14, -6.f * le.x * rinv8);
                 const float dphi_lj = fmaf(-168.f * le.y, rinv14 * rinv2, 48.f * le.x * rinv8 * rinv2);
                 const float qq = xi.w * xj[h].w;
-                float psi, dpsi, vcu;
+                float psi = 0.f, dpsi = 0.f, vcu = 0.f;
                 if (COUL == NB_COULOMB_RF) {
                     psi = f * fmaf(rinv, rinv2, -2.f * sv.k_rf);
                     dpsi = -3.f * f * rinv2 * rinv2 * rinv;
                     vcu = f * ((rinv - sv.c_rf) + fmaf(sv.k_rf, r2, -sv.c_rf_lo));
-                } else {
+                } else if (COUL == NB_COULOMB_EWALD) {
                     const float r = r2 * rinv;
                     const float z = sv.ew_beta * r;
                     const float ez = __expf(-z * z);
@@ -281,8 +281,10 @@ nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, f
         const int nb = (v.s.n_items + kVW - 1) / kVW;
         if (c->coulomb == NB_COULOMB_RF)
             k_vjp<NB_COULOMB_RF><<<nb, kVW * 32, 0, st>>>(v);
-        else
+        else if (c->coulomb == NB_COULOMB_EWALD)
             k_vjp<NB_COULOMB_EWALD><<<nb, kVW * 32, 0, st>>>(v);
+        else
+            k_vjp<NB_COULOMB_NONE><<<nb, kVW * 32, 0, st>>>(v);
     }
     const int nf = c->N > c->T * c->T ? c->N : c->T * c->T;
     k_vjp_finish<<<(nf + 255) / 256, 256, 0, st>>>(c->N, c->inv, c->gxs, c->gqs, gx, gq, c->T, c->gpar, gc6, gc12);

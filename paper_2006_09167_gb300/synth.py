@@ -36,6 +36,7 @@ MASS_H = 1.008
 
 COULOMB_RF = 0
 COULOMB_EWALD = 1
+COULOMB_NONE = 2  # Lennard-Jones only (argon)
 
 
 @dataclasses.dataclass
@@ -314,7 +315,7 @@ def argon_box(n_atoms: int = 1000, seed: int = 7, rho: float = 26.0, sigma: floa
     off, idx = csr_from_pairs(n_atoms, np.zeros((0, 2)))
     return System(name=f"argon_{n_atoms}", x=_wrap32(x, box), q=np.zeros(n_atoms, np.float32),
                   types=np.zeros(n_atoms, np.int32), c6=c6, c12=c12, excl_off=off, excl_idx=idx,
-                  box=box, coulomb=COULOMB_RF, rc=rc, rlist=rlist,
+                  box=box, coulomb=COULOMB_NONE, rc=rc, rlist=rlist,
                   r_in=rc if r_in is None else r_in, mass=np.full(n_atoms, 39.948))
 
 

@@ -68,7 +68,7 @@ def _params(**over):
 
 
 @pytest.mark.parametrize("over", [
-    dict(n_atoms=0), dict(n_types=0), dict(n_types=65), dict(coulomb=2), dict(reserved=1),
+    dict(n_atoms=0), dict(n_types=0), dict(n_types=65), dict(coulomb=3), dict(reserved=1),
     dict(eps_r=0.0), dict(rc=-1.0), dict(rc=9.0, rlist=9.5, r_in=9.0), dict(r_in=0.8),
     dict(rlist=0.85), dict(coulomb=1, beta=0.0), dict(coulomb=1, beta=5.0), dict(rc=float("nan")),
 ])

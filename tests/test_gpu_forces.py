@@ -212,3 +212,13 @@ def test_forces_1p5M_polymer_water_full_size(api):
     assert rms_rel(f, full["F"]) < TOL_F
     net = np.abs(f.astype(np.float64).sum(0)).max()
     assert net < TOL_NET * np.abs(f).sum()
+
+
+@pytest.mark.parametrize("n", [1000, 20000])
+def test_forces_argon_lj_only(api, n):
+    # LJ argon (no charges, Lennard-Jones-only kernel flavour) at the paper's density
+    s = synth.argon_box(n, seed=13, rc=1.1, rlist=1.2)
+    _, f, e, w = run_forces(api, s)
+    ref = oracle.celllist(s)
+    check_parity(s, ref, f, e, w)
+    assert e[1] == 0.0
