@@ -280,6 +280,7 @@ void nb_destroy(nb_ctx *c) {
     dfree(c->si_counts);
     dfree(c->si_offs);
     dfree(c->sort_tmp);
+    dfree(c->kept);
     dfree(c->diag);
     dfree(c->err);
     for (int k = 0; k < NB_TRACE_KINDS; k++) {
@@ -409,6 +410,7 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
         int cap = c->n_j + c->n_j / 8 + 64;
         if ((s = dalloc(&c->cj_outer, cap)) != NB_OK) return s;
         if ((s = dalloc(&c->cj_inner, cap)) != NB_OK) return s;
+        if ((s = dalloc(&c->kept, cap)) != NB_OK) return s;
         c->j_cap = cap;
     }
     if (c->n_masks > c->masks_cap) {
@@ -428,6 +430,7 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
         c->sort_tmp_cap = need_sort;
     }
     if ((s = nb_launch_search_write(c, rlist, st)) != NB_OK) return s;
+    c->split_built = c->split;
     c->rlist_built = rlist;
     if ((s = nb_launch_prune(c, (float)c->r_in, 0, 1, st)) != NB_OK) return s;
     NB_CUDA_TRY(cudaStreamSynchronize(st));

@@ -142,7 +142,8 @@ struct nb_ctx {
     // lists
     bool have_list = false;
     float rlist_built = 0.f;
-    int split = 32;          // max outer j-entries per work item
+    int split = 32;          // max outer j-entries per work item (next build)
+    int split_built = 32;    // max outer j-entries per work item of the current lists
     int n_items = 0, n_j = 0, n_masks = 0;
     int items_cap = 0, j_cap = 0, masks_cap = 0, si_cap = 0;
     int4 *items = nullptr, *items_tmp = nullptr;
@@ -152,6 +153,7 @@ struct nb_ctx {
     int *si_counts = nullptr;  // [3*si_cap]: j entries, items, mask groups per super-cluster
     int *si_offs = nullptr;    // [3*(si_cap+1)]
     int *sort_tmp = nullptr;   // item sort scratch
+    unsigned char *kept = nullptr;  // [j_cap] prune scratch: surviving mask byte per outer entry
     int sort_tmp_cap = 0;
     int64_t n_outer_bits = 0;
     // diagnostics

@@ -24,21 +24,30 @@ struct PruneArgs {
     float rin2;
     int2 *cj_inner;
     int *inner_len;
+    unsigned char *kept;  // [n_j] surviving mask byte per outer entry (scratch)
 };
 
-// One warp per item; the warp works on 4 entries at a time (8 lanes each, lane
-// t of a group owning i-atom t of every i-cluster) so that four entries' loads
-// are in flight together -- the loop is latency-bound otherwise.  Surviving
-// entries are compacted in their original order.
-__global__ void __launch_bounds__(kPW * 32) k_prune(PruneArgs a) {
+// The rolling prune runs as two kernels so that its parallelism does not depend
+// on the length of the work items:
+//  k_prune_masks: one warp per chunk of 16 outer entries of an item of this part;
+//    the warp works on 4 entries at a time (8 lanes each, lane t of a group owning
+//    i-atom t of every i-cluster) and writes each entry's surviving mask byte;
+//  k_prune_compact: one warp per item of this part copies the entries whose mask
+//    survived, in their original order, into the inner list.
+constexpr int kPruneChunk = 16;
+
+__global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunks_per_item) {
     __shared__ float4 s_xi[kPW][NB_SCA];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
     const long long w = (long long)blockIdx.x * kPW + wib;
-    const long long item = a.part + w * a.n_parts;
+    const long long item = a.part + (w / chunks_per_item) * a.n_parts;
     if (item >= a.n_items) return;
     const int4 it = a.items[item];
-    const int si = it.x, sidx = it.y, j0 = it.z, len = it.w;
+    const int e_begin = (int)(w % chunks_per_item) * kPruneChunk;
+    if (e_begin >= it.w) return;
+    const int e_end = min(it.w, e_begin + kPruneChunk);
+    const int si = it.x, sidx = it.y, j0 = it.z;
     const ShiftSplit sh = make_shift(sidx, a.Lhi, a.Llo);
     for (int h = 0; h < 2; h++) {
         int at = lane + 32 * h;
@@ -46,10 +55,9 @@ __global__ void __launch_bounds__(kPW * 32) k_prune(PruneArgs a) {
     }
     __syncwarp();
     const int g = lane >> 3, t = lane & 7;
-    int cnt = 0;
-    for (int e0 = 0; e0 < len; e0 += 4) {
+    for (int e0 = e_begin; e0 < e_end; e0 += 4) {
         const int e = e0 + g;
-        const bool valid = e < len;
+        const bool valid = e < e_end;
         const int2 ent = valid ? a.cj_outer[j0 + e] : make_int2(0, 0);
         const int im = ent.y & 0xff;
         float4 xj[NB_CL];
@@ -72,11 +80,29 @@ __global__ void __launch_bounds__(kPW * 32) k_prune(PruneArgs a) {
         kept |= __shfl_xor_sync(full, kept, 1);
         kept |= __shfl_xor_sync(full, kept, 2);
         kept |= __shfl_xor_sync(full, kept, 4);
-        const unsigned keep = __ballot_sync(full, t == 0 && kept != 0);
-        if (t == 0 && kept != 0) {
-            const int pos = cnt + __popc(keep & ((1u << lane) - 1));
-            a.cj_inner[j0 + pos] = make_int2(ent.x, (ent.y & ~0xff) | kept);
+        if (t == 0 && valid) a.kept[j0 + e] = (unsigned char)kept;
+    }
+}
+
+__global__ void __launch_bounds__(kPW * 32) k_prune_compact(PruneArgs a) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
+    const long long w = (long long)blockIdx.x * kPW + wib;
+    const long long item = a.part + w * a.n_parts;
+    if (item >= a.n_items) return;
+    const int4 it = a.items[item];
+    const int j0 = it.z, len = it.w;
+    int cnt = 0;
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        int kept = 0;
+        int2 ent = make_int2(0, 0);
+        if (e < len) {
+            kept = a.kept[j0 + e];
+            if (kept) ent = a.cj_outer[j0 + e];
         }
+        const unsigned keep = __ballot_sync(full, kept != 0);
+        if (kept) a.cj_inner[j0 + cnt + __popc(keep & ((1u << lane) - 1))] = make_int2(ent.x, (ent.y & ~0xff) | kept);
         cnt += __popc(keep);
     }
     if (lane == 0) a.inner_len[item] = cnt;
@@ -196,11 +222,15 @@ nb_status nb_launch_prune(nb_ctx *c, float r_in, int part, int n_parts, cudaStre
     a.rin2 = re * re;
     a.cj_inner = c->cj_inner;
     a.inner_len = c->inner_len;
+    a.kept = c->kept;
     long long nw = (c->n_items - part + n_parts - 1) / n_parts;
     if (nw <= 0) return NB_OK;
+    const int chunks = (c->split_built + kPruneChunk - 1) / kPruneChunk;
     NbTraceScope tr(c, NB_TRACE_PRUNE, st);
-    c->n_launches++;
-    k_prune<<<(unsigned)((nw + kPW - 1) / kPW), kPW * 32, 0, st>>>(a);
+    c->n_launches += 2;
+    const long long nwm = nw * chunks;
+    k_prune_masks<<<(unsigned)((nwm + kPW - 1) / kPW), kPW * 32, 0, st>>>(a, chunks);
+    k_prune_compact<<<(unsigned)((nw + kPW - 1) / kPW), kPW * 32, 0, st>>>(a);
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
 }
