@@ -390,6 +390,7 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
         c->si_cap = cap;
     }
     if (c->S_host == 0) return NB_ERR_NOT_READY;
+    if ((long long)c->S_host * NB_SCL >= (1ll << 24)) return NB_ERR_CAPACITY;  // 24-bit cluster index
     if ((s = nb_launch_search_count(c, rlist, st)) != NB_OK) return s;
     int tot[4];
     NB_CUDA_TRY(cudaMemcpyAsync(tot, c->si_offs + 4 * (size_t)c->S_host, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));

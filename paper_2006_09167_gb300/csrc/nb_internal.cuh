@@ -5,8 +5,11 @@
 //   perm[s] caller index of the atom in slot s, -1 for a padding slot
 // Pair lists:
 //   item  int4 {si, shift index, j_start, outer length}; inner length in inner_len[item]
-//   entry int2 {cj, meta}: meta bits 0..7 interaction mask (bit k: i-cluster k of si),
+//   outer entry int2 {cj, meta}: meta bits 0..7 interaction mask (bit k: i-cluster k of si),
 //         bits 8..31 = 1 + index of a group of 8 uint64 exclusion masks (0: none)
+//   inner entry int2: the prune keeps one bit per (i-cluster, j-half) (j-cluster splitting):
+//         x = cj | hi << 24, y = lo | (exclusion group + 1) << 8, where bit k of lo (hi) says
+//         that i-cluster k interacts with j-atoms 0..3 (4..7) of cj
 //   exclusion mask u64 per (i-cluster k, j-cluster): bit 8*a + b set = pair (i-atom a,
 //         j-atom b) interacts (cleared for excluded pairs, the lower triangle and padding
 //         of a self cluster pair).
@@ -61,6 +64,12 @@ struct SysView {
     float ew_shift;  // erfc(beta rc)/rc (without the Coulomb constant)
     float rc6inv, rc12inv;
 };
+
+// inner-entry decoding
+__host__ __device__ __forceinline__ int inner_cj(int2 e) { return e.x & 0xffffff; }
+__host__ __device__ __forceinline__ int inner_lo(int2 e) { return e.y & 0xff; }
+__host__ __device__ __forceinline__ int inner_hi(int2 e) { return (int)((unsigned)e.x >> 24); }
+__host__ __device__ __forceinline__ int entry_group(int2 e) { return (int)((unsigned)e.y >> 8); }
 
 __device__ __forceinline__ void record_error(int *flag, int code) {
     if (flag) atomicCAS(flag, 0, code);
@@ -153,7 +162,7 @@ struct nb_ctx {
     int *si_counts = nullptr;  // [3*si_cap]: j entries, items, mask groups per super-cluster
     int *si_offs = nullptr;    // [3*(si_cap+1)]
     int *sort_tmp = nullptr;   // item sort scratch
-    unsigned char *kept = nullptr;  // [j_cap] prune scratch: surviving mask byte per outer entry
+    unsigned short *kept = nullptr;  // [j_cap] prune scratch: surviving half masks per outer entry
     int sort_tmp_cap = 0;
     int64_t n_outer_bits = 0;
     // diagnostics

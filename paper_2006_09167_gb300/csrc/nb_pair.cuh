@@ -199,8 +199,8 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
 
     for (int e = 0; e < nj; e++) {
         const int2 ent = v.cj[j0 + e];
-        const int cj = ent.x, mg = ent.y >> 8;
-        int im = ent.y & 0xff;
+        const int cj = inner_cj(ent), mg = entry_group(ent);
+        const int lo = inner_lo(ent), hi = inner_hi(ent);
         float4 xj0 = v.xq[cj * NB_CL + tj], xj1 = v.xq[cj * NB_CL + tj + 4];
         if (sh.jshift) {
             xj0 = shift_j(xj0, sh);
@@ -209,10 +209,12 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
         const int tj0 = v.type[cj * NB_CL + tj], tj1 = v.type[cj * NB_CL + tj + 4];
         float f0x = 0.f, f0y = 0.f, f0z = 0.f, f1x = 0.f, f1y = 0.f, f1z = 0.f;
         float elj_e = 0.f, ec_e = 0.f;
+        // i-clusters that interact with both j-halves: two independent pairs per lane
+        int both = lo & hi;
 #pragma unroll 1
-        while (im) {
-            const int k = __ffs(im) - 1;
-            im &= im - 1;
+        while (both) {
+            const int k = __ffs(both) - 1;
+            both &= both - 1;
             bool b0 = true, b1 = true;
             if (mg) {
                 const unsigned long long m = v.masks[(size_t)(mg - 1) * 8 + k];
@@ -237,6 +239,38 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             f1x -= bx;
             f1y -= by;
             f1z -= bz;
+        }
+        // i-clusters that the prune kept for one j-half only: one pair per lane
+        int one = lo ^ hi;
+#pragma unroll 1
+        while (one) {
+            const int k = __ffs(one) - 1;
+            one &= one - 1;
+            const bool upper = (hi >> k) & 1;  // warp-uniform
+            bool b = true;
+            if (mg) {
+                const unsigned long long m = v.masks[(size_t)(mg - 1) * 8 + k];
+                b = (m >> (ti * 8 + tj + (upper ? 4 : 0))) & 1ull;
+            }
+            const float4 xj = upper ? xj1 : xj0;
+            const float4 xi = s_xi[k * NB_CL + ti];
+            const int tio = s_ti[k * NB_CL + ti];
+            const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
+            const float p = pair_phi<COUL, EN>(v, ljt, lje, d, xi.w, xj.w, tio + (upper ? tj1 : tj0), b, elj_e, ec_e);
+            const float ax = p * d.x, ay = p * d.y, az = p * d.z;
+            float *fk = s_fi + k * 96 + lane;
+            fk[0] += ax;
+            fk[32] += ay;
+            fk[64] += az;
+            if (upper) {
+                f1x -= ax;
+                f1y -= ay;
+                f1z -= az;
+            } else {
+                f0x -= ax;
+                f0y -= ay;
+                f0z -= az;
+            }
         }
         if (EN) {
             elj.add(elj_e);

@@ -24,7 +24,7 @@ struct PruneArgs {
     float rin2;
     int2 *cj_inner;
     int *inner_len;
-    unsigned char *kept;  // [n_j] surviving mask byte per outer entry (scratch)
+    unsigned short *kept;  // [n_j] surviving half masks (lo | hi << 8) per outer entry (scratch)
 };
 
 // The rolling prune runs as two kernels so that its parallelism does not depend
@@ -63,24 +63,28 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunk
         float4 xj[NB_CL];
 #pragma unroll
         for (int b = 0; b < NB_CL; b++) xj[b] = shift_j(a.xq[ent.x * NB_CL + b], sh);
-        int kept = 0;
+        int lo = 0, hi = 0;
 #pragma unroll
         for (int k = 0; k < NB_SCL; k++) {
             if (im & (1 << k)) {
                 const float4 xi = s_xi[wib][k * NB_CL + t];
-                bool any = false;
+                bool any0 = false, any1 = false;
 #pragma unroll
                 for (int b = 0; b < NB_CL; b++) {
                     const float dx = xi.x - xj[b].x, dy = xi.y - xj[b].y, dz = xi.z - xj[b].z;
-                    any |= fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < a.rin2;
+                    const bool in = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < a.rin2;
+                    if (b < 4) any0 |= in;
+                    else any1 |= in;
                 }
-                kept |= (int)any << k;
+                lo |= (int)any0 << k;
+                hi |= (int)any1 << k;
             }
         }
+        int kept = lo | (hi << 8);
         kept |= __shfl_xor_sync(full, kept, 1);
         kept |= __shfl_xor_sync(full, kept, 2);
         kept |= __shfl_xor_sync(full, kept, 4);
-        if (t == 0 && valid) a.kept[j0 + e] = (unsigned char)kept;
+        if (t == 0 && valid) a.kept[j0 + e] = (unsigned short)kept;
     }
 }
 
@@ -102,7 +106,9 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_compact(PruneArgs a) {
             if (kept) ent = a.cj_outer[j0 + e];
         }
         const unsigned keep = __ballot_sync(full, kept != 0);
-        if (kept) a.cj_inner[j0 + cnt + __popc(keep & ((1u << lane) - 1))] = make_int2(ent.x, (ent.y & ~0xff) | kept);
+        if (kept)
+            a.cj_inner[j0 + cnt + __popc(keep & ((1u << lane) - 1))] =
+                make_int2(ent.x | ((kept >> 8) << 24), (ent.y & ~0xff) | (kept & 0xff));
         cnt += __popc(keep);
     }
     if (lane == 0) a.inner_len[item] = cnt;
@@ -129,15 +135,20 @@ __global__ void __launch_bounds__(kPW * 32)
     __syncwarp();
     const int ti = lane & 7, tj = lane >> 3;
     unsigned long long within = 0, evald = 0;
+    const bool is_inner = inner_len != nullptr;
     for (int e = 0; e < len; e++) {
         const int2 ent = cj[it.z + e];
-        const int c = ent.x, im = ent.y & 0xff, mg = ent.y >> 8;
+        // outer entries: one mask bit per i-cluster for the whole j-cluster;
+        // inner entries: one bit per (i-cluster, j-half)
+        const int c = is_inner ? inner_cj(ent) : ent.x, mg = entry_group(ent);
+        const int lo = ent.y & 0xff, hi = is_inner ? inner_hi(ent) : lo;
         for (int k = 0; k < NB_SCL; k++) {
-            if (!(im & (1 << k))) continue;
-            evald += 2;
+            if (!((lo | hi) >> k & 1)) continue;
             const unsigned long long m = mg ? masks[(size_t)(mg - 1) * 8 + k] : ~0ull;
             const float4 xi = s_xi[wib][k * NB_CL + ti];
             for (int h = 0; h < 2; h++) {
+                if (!(((h ? hi : lo) >> k) & 1)) continue;
+                evald += 1;
                 const float4 xj = shift_j(xq[c * NB_CL + tj + 4 * h], sh);
                 float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
                 float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -170,14 +181,17 @@ __global__ void __launch_bounds__(kPW * 32)
     shift_of(it.y, sx, sy, sz);
     for (int e = 0; e < len; e++) {
         const int2 ent = cj[it.z + e];
-        const int c = ent.x, im = ent.y & 0xff, mg = ent.y >> 8;
+        const bool is_inner = inner_len != nullptr;
+        const int c = is_inner ? inner_cj(ent) : ent.x, mg = entry_group(ent);
+        const int lo = ent.y & 0xff, hi = is_inner ? inner_hi(ent) : lo;
         for (int k = 0; k < NB_SCL; k++) {
-            if (!(im & (1 << k))) continue;
+            if (!((lo | hi) >> k & 1)) continue;
             const unsigned long long m = mg ? masks[(size_t)(mg - 1) * 8 + k] : ~0ull;
             for (int h = 0; h < 2; h++) {
                 const int p = lane + 32 * h;  // p = 8*a + b
                 const int ia = p >> 3, jb = p & 7;
                 if (!((m >> p) & 1ull)) continue;
+                if (!((((jb < 4) ? lo : hi) >> k) & 1)) continue;
                 const int i = perm[it.x * NB_SCA + k * NB_CL + ia];
                 const int j = perm[c * NB_CL + jb];
                 if (i < 0 || j < 0) continue;

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v) {
 
     for (int e = 0; e < nj; e++) {
         const int2 ent = sv.cj[j0 + e];
-        const int cj = ent.x, im = ent.y & 0xff, mg = ent.y >> 8;
+        const int cj = inner_cj(ent), mg = entry_group(ent), lo = inner_lo(ent), hi = inner_hi(ent);
+        const int im = lo | hi;
         float4 xj[2], gj[2];
         int tjt[2];
         float ajx[2] = {0.f, 0.f}, ajy[2] = {0.f, 0.f}, ajz[2] = {0.f, 0.f}, ajq[2] = {0.f, 0.f};
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v) {
             const int ta = s_ti[wib][k * NB_CL + ti];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
+                if (!(((h ? hi : lo) >> k) & 1)) continue;  // j-half pruned away (warp-uniform)
                 const bool bit = (m >> (ti * 8 + tj + 4 * h)) & 1ull;
                 const float dx = xi.x - xj[h].x, dy = xi.y - xj[h].y, dz = xi.z - xj[h].z;
                 float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
