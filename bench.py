@@ -174,7 +174,7 @@ def run_ours(args, rank, world, local_rank):
     box = s.box
     from paper_2006_09167_gb300 import autotune
     # the work-item size is autotuned; the prune cadence is the workload's (2 rolling parts)
-    tuned = autotune.tune(s, x0)
+    tuned = autotune.tune(s, x0, flush=flush)
     ctx.nb_set_split(tuned["split"])
     n_parts = N_PARTS
     ctx.build(x0, box)
@@ -267,8 +267,10 @@ def extra_workloads(args):
     # batched: 256 uneven replicas
     reps = synth.replica_set()
     from paper_2006_09167_gb300 import autotune
-    med = sorted(reps, key=lambda r: r.n)[len(reps) // 2]
-    tuned_b = autotune.tune(med, torch.tensor(med.x, device=dev))
+    flush = l2_flusher(dev)
+    xs_tune = [torch.tensor(sysr.x, device=dev) for sysr in reps]
+    tuned_b = autotune.tune_batched(reps, xs_tune, splits=(8, 12, 16, 24, 32, 48, 64), reps=5, flush=flush)
+    del xs_tune
     ctxs, xs = [], []
     for sysr in reps:
         c = api.NbContext.from_system(sysr)
@@ -287,7 +289,6 @@ def extra_workloads(args):
     fs = [torch.empty_like(xr) for xr in xs]
     es = [torch.empty(2, dtype=torch.float64, device=dev) for _ in xs]
     ws = [torch.empty(9, dtype=torch.float64, device=dev) for _ in xs]
-    flush = l2_flusher(dev)
 
     def batched():
         b.nb_forces_batched(flags, xcat, fcat, e, w)
@@ -503,6 +504,8 @@ def main_profile(args):
     from paper_2006_09167_gb300 import api, synth
     s = synth.water_96k()
     ctx = api.NbContext.from_system(s)
+    if args.split:
+        ctx.nb_set_split(args.split)
     x = torch.tensor(s.x, device="cuda")
     ctx.build(x, s.box)
     f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
@@ -527,6 +530,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true",
                     help="profiling target: warmup + steps force evaluations (energy+virial) of the 96k box only")
+    ap.add_argument("--split", type=int, default=0,
+                    help="with --profile: the work-item split to build with (default: the library's)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

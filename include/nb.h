@@ -143,9 +143,11 @@ nb_status nb_pairlist_build(nb_ctx *ctx, float rlist, void *stream);
 
 /* Rolling prune (Sec. V.E): re-prune part `part` of `n_parts` interleaved
  * parts of the outer list against r_in (rc <= r_in <= rlist), using the
- * positions of the last nb_forces (or nb_grid_sort) call.  Keeps an
- * interaction-mask bit iff some atom pair of that cluster pair is closer than
- * r_in.  The outer list is unchanged.  Asynchronous; never allocates. */
+ * positions of the last nb_forces (or nb_grid_sort) call.  For each i-cluster
+ * and each half (atoms 0-3, 4-7) of the j-cluster it keeps a bit iff some atom
+ * pair of that 8x4 block is closer than r_in (j-cluster splitting); entries
+ * with no bit left are dropped.  The outer list is unchanged.  Asynchronous;
+ * never allocates. */
 nb_status nb_prune_rolling(nb_ctx *ctx, float r_in, int part, int n_parts, void *stream);
 
 /* Forces (Sec. V.A): gathers x_dev [N*3] (caller order) into the cluster
@@ -154,7 +156,9 @@ nb_status nb_prune_rolling(nb_ctx *ctx, float r_in, int part, int n_parts, void 
  * writes e_dev[2] = {E_LJ, E_Coulomb} (FP64, overwritten); NB_VIRIAL writes
  * vir_dev[9] (FP64 row-major, overwritten).  Pair arithmetic and force
  * accumulation are FP32; energies and virial are reduced in FP64.
- * Asynchronous; never allocates; may be captured in a CUDA graph. */
+ * Asynchronous; never allocates; may be captured in a CUDA graph.  Calls on
+ * one context (forces, prune, adjoint) must not overlap on the GPU: they share
+ * the context's layout, accumulators and work-item counter. */
 nb_status nb_forces(nb_ctx *ctx, unsigned flags, const float *x_dev, float *f_dev, double *e_dev,
                     double *vir_dev, void *stream);
 
@@ -184,8 +188,8 @@ nb_status nb_forces_batched(nb_batch *batch, unsigned flags, const float *x_dev,
 
 /* Counts over the inner (NB_LIST_INNER) or outer (NB_LIST_OUTER) list at the
  * current positions: pairs inside rc that the force kernel computes from it
- * (effective interactions) and atom pairs evaluated (8x8 per set mask bit, the
- * raw work).  Pairs inside rc that the outer list has and the inner list lacks
+ * (effective interactions) and atom pairs evaluated (the raw work: 8x8 per
+ * mask bit of an outer entry, 8x4 per half-mask bit of an inner entry).  Pairs inside rc that the outer list has and the inner list lacks
  * were missed by the prune.  Synchronises `stream`. */
 nb_status nb_count_pairs(nb_ctx *ctx, int which, int64_t *n_within_rc, int64_t *n_evaluated, void *stream);
 
@@ -207,7 +211,7 @@ nb_status nb_get_stats(nb_ctx *ctx, nb_stats *out);
 
 /* Tuning (Sec. V.F: lists are split when there are too few of them for the GPU):
  * the largest number of outer j-cluster entries per work item (4..128, default
- * 32).  Takes effect at the next nb_pairlist_build. */
+ * 16).  Takes effect at the next nb_pairlist_build. */
 nb_status nb_set_split(nb_ctx *ctx, int max_entries_per_item);
 
 /* Tracing (not in the paper): when enabled, CUDA events are recorded on the

@@ -20,9 +20,9 @@ from __future__ import annotations
 import hashlib
 import json
 import os
-from typing import Dict, Optional, Sequence
+from typing import Callable, Dict, Optional, Sequence
 
-SPLITS = (16, 24, 32, 48, 64, 96, 128)
+SPLITS = (8, 12, 16, 24, 32, 48, 64, 96, 128)
 PARTS = (1, 2, 4, 8)
 
 
@@ -69,11 +69,13 @@ def save_cache(path: Optional[str], cache: dict) -> None:
 
 def tune(system, x, velocities=None, *, splits: Sequence[int] = SPLITS, parts: Sequence[int] = PARTS,
          nstlist: int = 100, dt: float = 0.002, reps: int = 10, cache_path: Optional[str] = None,
-         flags: Optional[int] = None) -> dict:
+         flags: Optional[int] = None, flush: Optional[Callable[[], None]] = None) -> dict:
     """Tune split and n_parts for `system` at positions x (CUDA float32 [N,3]).
 
     velocities (CUDA [N,3], nm/ps) drive the ballistic trajectory of the prune
-    check; without them only `split` is tuned and n_parts is 2.
+    check; without them only `split` is tuned and n_parts is 2.  `flush`, when
+    given, is called before every timed evaluation (e.g. to evict the L2 cache
+    as the caller's own loop does), outside the timed kernel.
     """
     import torch
 
@@ -100,6 +102,8 @@ def tune(system, x, velocities=None, *, splits: Sequence[int] = SPLITS, parts: S
         torch.cuda.synchronize()
         ctx.nb_trace_read(api.NB_TRACE_FORCES)
         for _ in range(reps):
+            if flush is not None:
+                flush()
             ctx.nb_forces(flags, x, f, e, w)
         ms, n = ctx.nb_trace_read(api.NB_TRACE_FORCES)
         split_ms[sp] = ms / max(n, 1)
@@ -131,3 +135,48 @@ def tune(system, x, velocities=None, *, splits: Sequence[int] = SPLITS, parts: S
     cache[key] = result
     save_cache(cache_path, cache)
     return result
+
+
+def tune_batched(systems, xs, *, splits: Sequence[int] = SPLITS, reps: int = 10, flags: Optional[int] = None,
+                 flush: Optional[Callable[[], None]] = None) -> dict:
+    """Tune the split of a batched evaluation (nb_forces_batched) by timing the
+    batched launch itself over `systems` at positions `xs` (CUDA float32 [N_r,3]
+    each): the best item size for many systems sharing the GPU differs from the
+    best one for any of them alone.  Returns {"split", "split_ms"}."""
+    import torch
+
+    from . import api
+
+    if flags is None:
+        flags = api.NB_ENERGY | api.NB_VIRIAL
+    dev = xs[0].device
+    xcat = torch.cat(list(xs)).contiguous()
+    fcat = torch.empty_like(xcat)
+    r = len(systems)
+    e = torch.empty(2 * r, dtype=torch.float64, device=dev)
+    w = torch.empty(9 * r, dtype=torch.float64, device=dev)
+    split_ms = {}
+    for sp in splits:
+        ctxs = []
+        for s, xr in zip(systems, xs):
+            c = api.NbContext.from_system(s)
+            c.nb_set_split(sp)
+            c.build(xr, s.box)
+            ctxs.append(c)
+        b = api.NbBatch(ctxs)
+        for _ in range(3):
+            b.nb_forces_batched(flags, xcat, fcat, e, w)
+        tot = 0.0
+        for _ in range(reps):
+            if flush is not None:
+                flush()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            b.nb_forces_batched(flags, xcat, fcat, e, w)
+            t1.record()
+            t1.synchronize()
+            tot += t0.elapsed_time(t1)
+        split_ms[sp] = tot / reps
+        b.close()
+        del ctxs
+    return {"split": choose_split(split_ms), "split_ms": split_ms}

@@ -1,8 +1,10 @@
 /* Generated by gen_ewald_rational.py -- do not edit.
- * Rational approximations, z = beta r, of
- *   H(z) = (erf(z)/z - 2/sqrt(pi) exp(-z^2)) / z^2 and E(z) = erf(z)/z  (in s = z^2/ZMAX^2)
- *   X(z) = exp(z^2) erfc(z)                                              (in t = z/ZMAX)
- * on 0 <= z <= ZMAX (relative errors below are measured against mpmath).
+ * Rational approximations, z = beta r, on 0 <= z <= ZMAX of
+ *   H(z) = (erf(z)/z - 2/sqrt(pi) exp(-z^2)) / z^2   (in s = z^2/ZMAX^2)
+ *   X(z) = exp(z^2) erfc(z)                          (in t = z/ZMAX)
+ * and exp(w) = 1 + w (C1 + C2 w + ...) on |w| <= ln2/2 with the Cody-Waite
+ * constants of exp(-x) = 2^-n exp(-(x - n ln2)).
+ * Relative errors below are measured against mpmath / FP64.
  */
 #pragma once
 #define NB_EW_ZMAX 4.0f
@@ -19,18 +21,6 @@
 #define NB_EW_HQ3 88.59178924560547f
 #define NB_EW_HQ4 137.36947631835938f
 #define NB_EW_HQ5 136.4874267578125f
-/* E: degrees (5,5); fp64 max rel err 2.48e-08; fp32 Horner max rel err 3.52e-07, mean -1.23e-08 */
-#define NB_EW_EP0 1.1283791065216064f
-#define NB_EW_EP1 3.096602201461792f
-#define NB_EW_EP2 13.59368896484375f
-#define NB_EW_EP3 15.904327392578125f
-#define NB_EW_EP4 18.647218704223633f
-#define NB_EW_EP5 2.0830705165863037f
-#define NB_EW_EQ1 8.07761287689209f
-#define NB_EW_EQ2 29.528717041015625f
-#define NB_EW_EQ3 62.285369873046875f
-#define NB_EW_EQ4 77.6876449584961f
-#define NB_EW_EQ5 39.23380661010742f
 /* X: degrees (4,4); fp64 max rel err 1.1e-08; fp32 Horner max rel err 3.32e-07, mean 7.62e-09 */
 #define NB_EW_XP0 1.0f
 #define NB_EW_XP1 3.465115547180176f
@@ -41,3 +31,14 @@
 #define NB_EW_XQ2 25.840158462524414f
 #define NB_EW_XQ3 41.050724029541016f
 #define NB_EW_XQ4 28.053558349609375f
+/* exp: degree 7; fp64 max rel err 4.67e-11; fp32 exp(-x) on [0,16] max rel err 7.23e-08, mean -1.8e-10 */
+#define NB_EXP_LOG2E 1.4426950216293335f
+#define NB_EXP_LN2_HI 0.693145751953125f
+#define NB_EXP_LN2_LO 1.428606765330187e-06f
+#define NB_EXP_C1 1.0f
+#define NB_EXP_C2 0.5f
+#define NB_EXP_C3 0.1666666567325592f
+#define NB_EXP_C4 0.04166627302765846f
+#define NB_EXP_C5 0.008333568461239338f
+#define NB_EXP_C6 0.0013945897808298469f
+#define NB_EXP_C7 0.0001976766943698749f

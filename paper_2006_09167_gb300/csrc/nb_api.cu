@@ -115,6 +115,9 @@ nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     double rc6 = 1.0 / (rc3 * rc3);
     v.rc6inv = (float)rc6;
     v.rc12inv = (float)(rc6 * rc6);
+    v.queue = c->queue;
+    v.ew_beta2 = (float)(c->beta * c->beta);
+    v.ew_2bsp = (float)(2.0 * c->beta / sqrt(M_PI));
     return v;
 }
 
@@ -216,6 +219,7 @@ nb_status nb_create(const nb_params *p, const float *q_host, const int32_t *type
     NB_TRY_ALLOC(dalloc(&c->counters, 16));
     NB_TRY_ALLOC(dalloc(&c->diag, 4));
     NB_TRY_ALLOC(dalloc(&c->err, 1));
+    NB_TRY_ALLOC(dalloc(&c->queue, 1));
     NB_TRY_ALLOC(dalloc(&c->col_of, N));
     NB_TRY_ALLOC(dalloc(&c->rank_of, N));
     NB_TRY_ALLOC(dalloc(&c->colbuf, N));
@@ -232,6 +236,9 @@ nb_status nb_create(const nb_params *p, const float *q_host, const int32_t *type
     if (e == cudaSuccess) e = cudaMemcpy(c->lj, lj.data(), sizeof(float2) * T * T, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->lje, lje.data(), sizeof(float4) * T * T, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
         nb_destroy(c);
         return nb_cuda_status(e);
@@ -283,6 +290,7 @@ void nb_destroy(nb_ctx *c) {
     dfree(c->kept);
     dfree(c->diag);
     dfree(c->err);
+    dfree(c->queue);
     for (int k = 0; k < NB_TRACE_KINDS; k++) {
         for (auto e : c->ev_start[k]) cudaEventDestroy(e);
         for (auto e : c->ev_end[k]) cudaEventDestroy(e);

@@ -45,32 +45,35 @@ __global__ void __launch_bounds__(kBW * 32)
     __shared__ float s_fi[kBW][3 * NB_SCL * 32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
-    for (;;) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(queue, 1);
-        g = __shfl_sync(full, g, 0);
-        if (g >= total) break;
+    // first item: the warp's index in the grid; later items from the counter
+    const int n_warps = gridDim.x * kBW;
+    int g = blockIdx.x * kBW + wib;
+    while (g < total) {
         const int2 m = gmap[g];
         const SysView &v = views[m.x];
         const int nj = v.inner_len[m.y];
-        if (nj == 0) continue;
-        KSum elj, ec;
-        float vr[9];
+        if (nj > 0) {
+            KSum elj, ec;
+            float vr[9];
 #pragma unroll
-        for (int k = 0; k < 9; k++) vr[k] = 0.f;
-        process_item<COUL, EN, VIR>(v, m.y, nj, v.lj, v.lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
-        __syncwarp();
-        if (EN || VIR) {
-            warp_reduce_outputs<EN, VIR>(elj, ec, vr);
-            if (lane == 0) {
-                if (EN) {
-                    atomicAdd(&e[2 * m.x], (double)elj.s - (double)elj.c);
-                    atomicAdd(&e[2 * m.x + 1], reps[m.x].coul_f * ((double)ec.s - (double)ec.c));
+            for (int k = 0; k < 9; k++) vr[k] = 0.f;
+            process_item<COUL, EN, VIR>(v, m.y, nj, v.lj, v.lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
+            __syncwarp();
+            if (EN || VIR) {
+                warp_reduce_outputs<EN, VIR>(elj, ec, vr);
+                if (lane == 0) {
+                    if (EN) {
+                        atomicAdd(&e[2 * m.x], (double)elj.s - (double)elj.c);
+                        atomicAdd(&e[2 * m.x + 1], reps[m.x].coul_f * ((double)ec.s - (double)ec.c));
+                    }
+                    if (VIR)
+                        for (int k = 0; k < 9; k++) atomicAdd(&vir[9 * m.x + k], -0.5 * (double)vr[k]);
                 }
-                if (VIR)
-                    for (int k = 0; k < 9; k++) atomicAdd(&vir[9 * m.x + k], -0.5 * (double)vr[k]);
             }
         }
+        int claim = 0;
+        if (lane == 0) claim = atomicAdd(queue, 1);
+        g = n_warps + __shfl_sync(full, claim, 0);
     }
 }
 

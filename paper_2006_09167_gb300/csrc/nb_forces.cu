@@ -20,6 +20,8 @@
 // Ewald real space: phi_C = f qi qj (1/r^3 - beta^3 H(z)), V_C = f qi qj (1/r -
 // beta E(z) - erfc(beta rc)/rc) with z = beta r, evaluated with the FMA-only
 // rational approximations of ewald_rational.h plus one fast reciprocal.
+#include <algorithm>
+
 #include "nb_pair.cuh"
 
 using namespace nbk;
@@ -28,6 +30,9 @@ namespace {
 
 constexpr int kFW = 4;  // warps (work items) per block
 
+// Persistent: a grid sized to the resident capacity of the GPU, each warp taking
+// the next work item (ordered longest first) from a device counter, so the
+// kernel tail is at most one item long (paper Sec. V.F: tails from uneven work).
 template <int COUL, bool EN, bool VIR>
 __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
     extern __shared__ float4 s_dyn[];
@@ -42,25 +47,34 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int w = blockIdx.x * kFW + wib;
-    if (w >= v.n_items) return;
-    const int nj = v.inner_len[w];
-    KSum elj, ec;
-    float vr[9];
+    const unsigned full = 0xffffffffu;
+    // first item: the warp's index in the grid; later items from the counter,
+    // which the gather zeroed (no burst of atomics at launch)
+    const int n_warps = gridDim.x * kFW;
+    int w = blockIdx.x * kFW + wib;
+    while (w < v.n_items) {
+        const int nj = v.inner_len[w];
+        KSum elj, ec;
+        float vr[9];
 #pragma unroll
-    for (int k = 0; k < 9; k++) vr[k] = 0.f;
-    if (nj > 0) process_item<COUL, EN, VIR>(v, w, nj, s_lj, s_lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
-    if (EN || VIR) {
-        // FP32 warp reduction; one row of 11 partial sums per work item, reduced in
-        // FP64 by the unsort kernel (no block barrier, no same-address atomics)
-        warp_reduce_outputs<EN, VIR>(elj, ec, vr);
-        if (lane < 11) {
-            double val;
-            if (lane == 0) val = (double)elj.s - (double)elj.c;
-            else if (lane == 1) val = (double)ec.s - (double)ec.c;
-            else val = (double)vr[lane - 2];
-            v.part[(size_t)w * 11 + lane] = val;
+        for (int k = 0; k < 9; k++) vr[k] = 0.f;
+        if (nj > 0) process_item<COUL, EN, VIR>(v, w, nj, s_lj, s_lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
+        if (EN || VIR) {
+            // FP32 warp reduction; one row of 11 partial sums per work item, reduced in
+            // FP64 by the unsort kernel (no block barrier, no same-address atomics)
+            warp_reduce_outputs<EN, VIR>(elj, ec, vr);
+            if (lane < 11) {
+                double val;
+                if (lane == 0) val = (double)elj.s - (double)elj.c;
+                else if (lane == 1) val = (double)ec.s - (double)ec.c;
+                else val = (double)vr[lane - 2];
+                v.part[(size_t)w * 11 + lane] = val;
+            }
         }
+        __syncwarp();  // this warp's staging arrays are reused by its next item
+        int claim = 0;
+        if (lane == 0) claim = atomicAdd(v.queue, 1);
+        w = n_warps + __shfl_sync(full, claim, 0);
     }
 }
 
@@ -69,9 +83,10 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
 __global__ void k_gather(int nslots, const int *__restrict__ perm, const float *__restrict__ x,
                          const int *__restrict__ img, const float *__restrict__ q_s, double Lx, double Ly,
                          double Lz, float4 *__restrict__ xq, float4 *__restrict__ fs, double *e, double *vir,
-                         int *err) {
+                         int *err, int *queue) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s == 0) {
+        *queue = 0;
         if (e) e[0] = e[1] = 0.0;
         if (vir)
             for (int k = 0; k < 9; k++) vir[k] = 0.0;
@@ -134,9 +149,14 @@ __global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__res
 }
 
 template <int COUL, bool EN, bool VIR>
-void launch_forces_t(const SysView &v, cudaStream_t st) {
-    size_t smem = (sizeof(float2) + (EN ? sizeof(float4) : 0)) * v.T * v.T;
-    k_forces<COUL, EN, VIR><<<(v.n_items + kFW - 1) / kFW, kFW * 32, smem, st>>>(v);
+void launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
+    const size_t smem = (sizeof(float2) + (EN ? sizeof(float4) : 0)) * v.T * v.T;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_forces<COUL, EN, VIR>, kFW * 32, smem) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    const int blocks = std::min((v.n_items + kFW - 1) / kFW, std::max(n_sm, 1) * occ);
+    k_forces<COUL, EN, VIR><<<blocks, kFW * 32, smem, st>>>(v);
 }
 
 }  // namespace
@@ -146,28 +166,28 @@ nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cu
     NbTraceScope tr(c, NB_TRACE_GATHER, st);
     c->n_launches++;
     k_gather<<<(ns + 255) / 256, 256, 0, st>>>(ns, c->perm, x, c->img, c->q_s, c->box[0], c->box[1],
-                                                c->box[2], c->xq, c->fs, e, vir, c->err);
+                                                c->box[2], c->xq, c->fs, e, vir, c->err, c->queue);
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
 }
 
-void nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, cudaStream_t st) {
+void nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, int n_sm, cudaStream_t st) {
     const bool en = flags & NB_ENERGY, vi = flags & NB_VIRIAL;
     if (coulomb == NB_COULOMB_RF) {
-        if (en && vi) launch_forces_t<NB_COULOMB_RF, true, true>(v, st);
-        else if (en) launch_forces_t<NB_COULOMB_RF, true, false>(v, st);
-        else if (vi) launch_forces_t<NB_COULOMB_RF, false, true>(v, st);
-        else launch_forces_t<NB_COULOMB_RF, false, false>(v, st);
+        if (en && vi) launch_forces_t<NB_COULOMB_RF, true, true>(v, n_sm, st);
+        else if (en) launch_forces_t<NB_COULOMB_RF, true, false>(v, n_sm, st);
+        else if (vi) launch_forces_t<NB_COULOMB_RF, false, true>(v, n_sm, st);
+        else launch_forces_t<NB_COULOMB_RF, false, false>(v, n_sm, st);
     } else if (coulomb == NB_COULOMB_EWALD) {
-        if (en && vi) launch_forces_t<NB_COULOMB_EWALD, true, true>(v, st);
-        else if (en) launch_forces_t<NB_COULOMB_EWALD, true, false>(v, st);
-        else if (vi) launch_forces_t<NB_COULOMB_EWALD, false, true>(v, st);
-        else launch_forces_t<NB_COULOMB_EWALD, false, false>(v, st);
+        if (en && vi) launch_forces_t<NB_COULOMB_EWALD, true, true>(v, n_sm, st);
+        else if (en) launch_forces_t<NB_COULOMB_EWALD, true, false>(v, n_sm, st);
+        else if (vi) launch_forces_t<NB_COULOMB_EWALD, false, true>(v, n_sm, st);
+        else launch_forces_t<NB_COULOMB_EWALD, false, false>(v, n_sm, st);
     } else {
-        if (en && vi) launch_forces_t<NB_COULOMB_NONE, true, true>(v, st);
-        else if (en) launch_forces_t<NB_COULOMB_NONE, true, false>(v, st);
-        else if (vi) launch_forces_t<NB_COULOMB_NONE, false, true>(v, st);
-        else launch_forces_t<NB_COULOMB_NONE, false, false>(v, st);
+        if (en && vi) launch_forces_t<NB_COULOMB_NONE, true, true>(v, n_sm, st);
+        else if (en) launch_forces_t<NB_COULOMB_NONE, true, false>(v, n_sm, st);
+        else if (vi) launch_forces_t<NB_COULOMB_NONE, false, true>(v, n_sm, st);
+        else launch_forces_t<NB_COULOMB_NONE, false, false>(v, n_sm, st);
     }
 }
 
@@ -178,7 +198,7 @@ nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, doubl
     SysView v = nb_make_view(c, c->fs, (flags & NB_ENERGY) ? e : nullptr, (flags & NB_VIRIAL) ? vir : nullptr);
     if (v.n_items > 0) {
         NbTraceScope tr(c, NB_TRACE_FORCES, st);
-        nb_dispatch_forces(v, c->coulomb, flags, st);
+        nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
         c->n_launches++;
     }
     const int nb = (c->N + 255) / 256;

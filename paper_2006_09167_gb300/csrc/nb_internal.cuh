@@ -62,7 +62,10 @@ struct SysView {
     float ew_beta3;  // beta^3
     float ew_beta;   // beta
     float ew_shift;  // erfc(beta rc)/rc (without the Coulomb constant)
+    float ew_beta2;  // beta^2
+    float ew_2bsp;   // 2 beta / sqrt(pi)
     float rc6inv, rc12inv;
+    int *queue;  // work-item counter of the persistent force kernel (zeroed by the gather)
 };
 
 // inner-entry decoding
@@ -151,8 +154,8 @@ struct nb_ctx {
     // lists
     bool have_list = false;
     float rlist_built = 0.f;
-    int split = 32;          // max outer j-entries per work item (next build)
-    int split_built = 32;    // max outer j-entries per work item of the current lists
+    int split = 16;          // max outer j-entries per work item (next build)
+    int split_built = 16;    // max outer j-entries per work item of the current lists
     int n_items = 0, n_j = 0, n_masks = 0;
     int items_cap = 0, j_cap = 0, masks_cap = 0, si_cap = 0;
     int4 *items = nullptr, *items_tmp = nullptr;
@@ -168,6 +171,8 @@ struct nb_ctx {
     // diagnostics
     long long *diag = nullptr;  // [4]
     int *err = nullptr;
+    int *queue = nullptr;  // work-item counter of the persistent force kernel
+    int n_sm = 0;          // multiprocessors of the context's device
     long long n_launches = 0;
     // tracing: event pairs per traced kernel kind
     bool trace = false;

@@ -25,22 +25,25 @@ __device__ __forceinline__ float ew_h(float s) {
     return __fdividef(p, q);
 }
 
-__device__ __forceinline__ float ew_e(float s) {
-    float p = fmaf(NB_EW_EP5, s, NB_EW_EP4);
-    p = fmaf(p, s, NB_EW_EP3);
-    p = fmaf(p, s, NB_EW_EP2);
-    p = fmaf(p, s, NB_EW_EP1);
-    p = fmaf(p, s, NB_EW_EP0);
-    float q = fmaf(NB_EW_EQ5, s, NB_EW_EQ4);
-    q = fmaf(q, s, NB_EW_EQ3);
-    q = fmaf(q, s, NB_EW_EQ2);
-    q = fmaf(q, s, NB_EW_EQ1);
-    q = fmaf(q, s, 1.0f);
-    return __fdividef(p, q);
+// exp(-x) for 0 <= x < 80: x = n ln2 + u (Cody-Waite reduction; n * LN2_HI is
+// exact), exp(-u) by the degree-7 polynomial 1 + w q(w) with w = -u, times 2^-n
+__device__ __forceinline__ float ew_expm(float x) {
+    const float n = rintf(x * NB_EXP_LOG2E);
+    float u = fmaf(-n, NB_EXP_LN2_HI, x);
+    u = fmaf(-n, NB_EXP_LN2_LO, u);
+    const float w = -u;
+    float q = fmaf(NB_EXP_C7, w, NB_EXP_C6);
+    q = fmaf(q, w, NB_EXP_C5);
+    q = fmaf(q, w, NB_EXP_C4);
+    q = fmaf(q, w, NB_EXP_C3);
+    q = fmaf(q, w, NB_EXP_C2);
+    q = fmaf(q, w, NB_EXP_C1);
+    const float p = fmaf(q, w, 1.0f);
+    return p * __int_as_float((127 - (int)n) << 23);
 }
 
-// erfc(z) = exp(-z^2) X(z), X the scaled complementary error function (rational in z/ZMAX)
-__device__ __forceinline__ float ew_erfc(float z) {
+// X(z) = exp(z^2) erfc(z), rational in t = z / ZMAX
+__device__ __forceinline__ float ew_x(float z) {
     const float t = z * (1.0f / NB_EW_ZMAX);
     float p = fmaf(NB_EW_XP4, t, NB_EW_XP3);
     p = fmaf(p, t, NB_EW_XP2);
@@ -50,7 +53,7 @@ __device__ __forceinline__ float ew_erfc(float z) {
     q = fmaf(q, t, NB_EW_XQ2);
     q = fmaf(q, t, NB_EW_XQ1);
     q = fmaf(q, t, 1.0f);
-    return __expf(-z * z) * __fdividef(p, q);
+    return __fdividef(p, q);
 }
 
 // Periodic shift of a work item split between the two sides of each pair so
@@ -134,11 +137,18 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
     const float2 lj = ljt[tpair];  // (6 C6, 12 C12)
     const float flj = rinv6 * fmaf(lj.y, rinv6, -lj.x);
     const float qq = qi * qj;
-    float fc = 0.f;
+    float fc = 0.f, erfcz = 0.f;
     if (COUL == NB_COULOMB_RF) {
         fc = qq * fmaf(rinv, rinv2, -2.0f * v.k_rf);
     } else if (COUL == NB_COULOMB_EWALD) {
-        fc = qq * fmaf(rinv, rinv2, -v.ew_beta3 * ew_h(r2 * v.ew_s));
+        if (EN) {
+            // one exp(-z^2) serves the energy, erfc(z) = exp(-z^2) X(z), and the force
+            const float ex = ew_expm(r2 * v.ew_beta2);
+            erfcz = ex * ew_x(v.ew_beta * (r2 * rinv));
+            fc = qq * rinv2 * fmaf(erfcz, rinv, v.ew_2bsp * ex);
+        } else {
+            fc = qq * fmaf(rinv, rinv2, -v.ew_beta3 * ew_h(r2 * v.ew_s));
+        }
     }
     if (EN) fc *= v.coul_f;
     float phi = fmaf(flj, rinv2, fc);
@@ -156,9 +166,7 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
             const float rlo = 0.5f * rinv * e;
             vc = (rinv - v.c_rf) + (fmaf(v.k_rf, r2, -v.c_rf_lo) + rlo);
         } else if (COUL == NB_COULOMB_EWALD) {
-            // CUDA's erfcf: measured against FP64 erfc it has the smallest bias of the
-            // variants tried (the energy totals of water sum 10^5-10^7 cancelling terms)
-            vc = fmaf(erfcf(v.ew_beta * (r2 * rinv)), rinv, -v.ew_shift);
+            vc = fmaf(erfcz, rinv, -v.ew_shift);
         }
         elj += in ? vlj : 0.f;
         ec += in ? qq * vc : 0.f;
@@ -289,19 +297,21 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             vr[7] += uz * f0y + wz * f1y;
             vr[8] += uz * f0z + wz * f1z;
         }
+        // j-force reduction over the 8 i-lanes, transposed: partners ti and ti ^ 4
+        // swap halves (lanes ti < 4 keep j-atom tj, lanes ti >= 4 keep tj + 4), then
+        // a butterfly over the remaining 4 lanes sums one atom per lane group
+        const bool upper = ti & 4;
+        float kx = upper ? f1x : f0x, ky = upper ? f1y : f0y, kz = upper ? f1z : f0z;
+        kx += __shfl_xor_sync(full, upper ? f0x : f1x, 4);
+        ky += __shfl_xor_sync(full, upper ? f0y : f1y, 4);
+        kz += __shfl_xor_sync(full, upper ? f0z : f1z, 4);
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            f0x += __shfl_xor_sync(full, f0x, o);
-            f0y += __shfl_xor_sync(full, f0y, o);
-            f0z += __shfl_xor_sync(full, f0z, o);
-            f1x += __shfl_xor_sync(full, f1x, o);
-            f1y += __shfl_xor_sync(full, f1y, o);
-            f1z += __shfl_xor_sync(full, f1z, o);
+        for (int o = 1; o < 4; o <<= 1) {
+            kx += __shfl_xor_sync(full, kx, o);
+            ky += __shfl_xor_sync(full, ky, o);
+            kz += __shfl_xor_sync(full, kz, o);
         }
-        if (ti == 0) {
-            atomicAdd(&v.f[cj * NB_CL + tj], make_float4(f0x, f0y, f0z, 0.f));
-            atomicAdd(&v.f[cj * NB_CL + tj + 4], make_float4(f1x, f1y, f1z, 0.f));
-        }
+        if ((ti & 3) == 0) atomicAdd(&v.f[cj * NB_CL + tj + (upper ? 4 : 0)], make_float4(kx, ky, kz, 0.f));
     }
     __syncwarp();
 #pragma unroll

@@ -54,3 +54,34 @@ def test_tune_on_gpu_gives_a_valid_correct_configuration(tmp_path):
     ctx.build(x, s.box)
     f, e, w = ctx.forces(x, energy=True, virial=True)
     assert rms_rel(f.cpu().numpy(), oracle.celllist(s)["F"]) < TOL_F
+
+
+@pytest.mark.gpu
+def test_tune_batched_times_the_batched_launch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_09167_gb300 import api
+    systems = [synth.water_box(n, 9.86 * (n / 32000) ** (1 / 3), seed=200 + n, rc=1.0, rlist=1.1)
+               for n in (1000, 1500, 2500)]
+    xs = [torch.tensor(s.x, device="cuda") for s in systems]
+    res = autotune.tune_batched(systems, xs, splits=(8, 16, 32), reps=2)
+    assert res["split"] in (8, 16, 32)
+    assert set(res["split_ms"]) == {8, 16, 32} and all(t > 0 for t in res["split_ms"].values())
+    # the tuned split evaluates the batch like the plain contexts do
+    ctxs = []
+    for s, xr in zip(systems, xs):
+        c = api.NbContext.from_system(s)
+        c.nb_set_split(res["split"])
+        c.build(xr, s.box)
+        ctxs.append(c)
+    b = api.NbBatch(ctxs)
+    xcat = torch.cat(xs).contiguous()
+    fcat = torch.empty_like(xcat)
+    e = torch.empty(6, dtype=torch.float64, device="cuda")
+    b.nb_forces_batched(api.NB_ENERGY, xcat, fcat, e)
+    for k, (c, xr) in enumerate(zip(ctxs, xs)):
+        f, ek, _ = c.forces(xr, energy=True)
+        o = int(b.offsets[k])
+        assert torch.allclose(fcat[o:o + len(xr)], f, rtol=0, atol=1e-3)
+        assert torch.allclose(e[2 * k:2 * k + 2], ek, rtol=1e-9, atol=0)
