@@ -1,4 +1,4 @@
-"""ctypes binding of the FP64 oracle in oracle.c (test infrastructure only).
+"""ctypes binding of the FP64 oracle in oracle.c and ewald.c (test infrastructure only).
 
 Inputs are the caller's arrays promoted exactly to float64 (float32 values are
 exactly representable), so the oracle evaluates the same system the CUDA
@@ -14,7 +14,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "ewald.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -24,11 +24,11 @@ _l = ctypes.POINTER(ctypes.c_int64)
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (-O2, OpenMP, no fast-math) into liboracle.so."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile oracle.c and ewald.c with gcc (-O2, OpenMP, no fast-math) into liboracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(p) for p in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
-                               "-D_GNU_SOURCE", _SRC, "-o", tmp, "-lm"])
+                               "-D_GNU_SOURCE"] + _SRCS + ["-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -54,6 +54,12 @@ def _load():
                                          _d, _d, _d]
         _lib.or_energy_moments.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double,
                                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _d]
+        _lib.or_ewald_recip.argtypes = [ctypes.c_int, _d, _d, _d, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, _d, _d]
+        _lib.or_ewald_excl.argtypes = [ctypes.c_int, _d, _d, _d, _i, _i, ctypes.c_double, ctypes.c_double,
+                                       _d, _d, _d]
+        _lib.or_ewald_self.argtypes = [ctypes.c_int, _d, ctypes.c_double, ctypes.c_double]
+        _lib.or_ewald_self.restype = ctypes.c_double
         _lib.or_num_threads.restype = ctypes.c_int
         _lib.or_set_num_threads.argtypes = [ctypes.c_int]
     return _lib
@@ -225,3 +231,51 @@ def num_threads() -> int:
 
 def set_num_threads(t: int) -> None:
     _load().or_set_num_threads(int(t))
+
+
+def ewald_kmax(box, beta: float, tol: float = 1e-12):
+    """Per-axis k-vector range beyond which the terms exp(-k^2/(4 beta^2)) are below tol."""
+    kcut = 2.0 * beta * math.sqrt(-math.log(tol))
+    return tuple(int(math.ceil(kcut * L / (2.0 * math.pi))) for L in np.asarray(box, np.float64))
+
+
+def ewald_recip(s, x=None, kmax=None, beta=None):
+    """Direct reciprocal-space Ewald sum (the plain definition PME approximates):
+    dict(F, E, W).  kmax per axis defaults to ewald_kmax(box, beta)."""
+    lib = _load()
+    xx = np.ascontiguousarray(s.x if x is None else x, dtype=np.float64)
+    q = np.ascontiguousarray(s.q, dtype=np.float64)
+    box = np.ascontiguousarray(s.box, dtype=np.float64)
+    b = float(s.beta if beta is None else beta)
+    if kmax is None:
+        kmax = ewald_kmax(s.box, b)
+    F = np.zeros((s.n, 3))
+    E = np.zeros(1)
+    W = np.zeros(9)
+    rc = lib.or_ewald_recip(s.n, _p(xx, _d), _p(q, _d), _p(box, _d), b, float(s.eps_r),
+                            int(kmax[0]), int(kmax[1]), int(kmax[2]), _p(F, _d), _p(E, _d), _p(W, _d))
+    if rc != 0:
+        raise RuntimeError(f"or_ewald_recip failed ({rc})")
+    return dict(F=F, E=float(E[0]), W=W.reshape(3, 3))
+
+
+def ewald_excl(s, x=None, beta=None):
+    """Exclusion correction -f qi qj erf(beta r)/r over the excluded pairs: dict(F, E, W)."""
+    lib = _load()
+    xx, q, _, _, _, off, idx, box = _arrays(s)
+    if x is not None:
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+    F = np.zeros((s.n, 3))
+    E = np.zeros(1)
+    W = np.zeros(9)
+    rc = lib.or_ewald_excl(s.n, _p(xx, _d), _p(q, _d), _p(box, _d), _p(off, _i), _p(idx, _i),
+                           float(s.beta if beta is None else beta), float(s.eps_r), _p(F, _d), _p(E, _d), _p(W, _d))
+    if rc != 0:
+        raise RuntimeError(f"or_ewald_excl failed ({rc})")
+    return dict(F=F, E=float(E[0]), W=W.reshape(3, 3))
+
+
+def ewald_self(s, beta=None):
+    """Self energy -f beta/sqrt(pi) sum q^2."""
+    q = np.ascontiguousarray(s.q, dtype=np.float64)
+    return float(_load().or_ewald_self(s.n, _p(q, _d), float(s.beta if beta is None else beta), float(s.eps_r)))

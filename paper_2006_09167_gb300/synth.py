@@ -296,6 +296,39 @@ def replica_set(n_rep: int = 256, seed: int = 5, mol_min: int = 1000, mol_max: i
     return systems
 
 
+def ionic_crystal(kind: str = "NaCl", a: float = 0.5640, cells: int = 2, beta: float = 8.0,
+                  rc: Optional[float] = None, origin=(0.1, 0.1, 0.1)) -> System:
+    """A perfect ionic crystal of unit charges in a cubic box of `cells`^3 conventional
+    cells (lattice constant a, nm): "NaCl" (rock salt, 8 ions per cell) or "CsCl"
+    (simple cubic pair, 2 ions per cell).  No Lennard-Jones, no exclusions, Ewald
+    electrostatics with the given beta; rc just below L/2.  Used to check the Ewald
+    sum against the known Madelung constants."""
+    if kind == "NaCl":
+        basis = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0],
+                          [.5, .5, .5], [.5, 0, 0], [0, .5, 0], [0, 0, .5]])
+        charge = np.array([1, 1, 1, 1, -1, -1, -1, -1], np.float64)
+    elif kind == "CsCl":
+        basis = np.array([[0, 0, 0], [.5, .5, .5]])
+        charge = np.array([1, -1], np.float64)
+    else:
+        raise ValueError(kind)
+    g = np.arange(cells)
+    cell = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    x = ((cell[:, None, :] + basis[None, :, :]) * a).reshape(-1, 3) + np.asarray(origin)
+    q = np.tile(charge, len(cell))
+    L = cells * a
+    box = np.full(3, L)
+    x = np.mod(x, L)
+    n = x.shape[0]
+    off = np.zeros(n + 1, np.int32)
+    return System(name=f"{kind.lower()}_{cells}", x=x.astype(np.float32), q=q.astype(np.float32),
+                  types=np.zeros(n, np.int32), c6=np.zeros((1, 1), np.float32),
+                  c12=np.zeros((1, 1), np.float32), excl_off=off, excl_idx=np.zeros(0, np.int32), box=box,
+                  coulomb=COULOMB_EWALD, rc=(0.499 * L if rc is None else rc),
+                  rlist=(0.499 * L if rc is None else rc), r_in=(0.499 * L if rc is None else rc),
+                  beta=beta, mass=np.full(n, 30.0))
+
+
 def argon_box(n_atoms: int = 1000, seed: int = 7, rho: float = 26.0, sigma: float = 0.3345,
               eps: float = 0.996, rc: float = 0.9, rlist: float = 1.0, r_in: Optional[float] = None,
               jitter: float = 0.01) -> System:
