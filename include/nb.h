@@ -52,6 +52,7 @@ extern "C" {
 
 typedef struct nb_ctx nb_ctx;
 typedef struct nb_batch nb_batch;
+typedef struct nb_pme nb_pme;
 
 typedef enum {
     NB_OK = 0,
@@ -230,6 +231,52 @@ nb_status nb_trace_read(nb_ctx *ctx, int kind, double *total_ms, int64_t *n_laun
 nb_status nb_get_error(nb_ctx *ctx, void *stream);
 
 const char *nb_status_str(nb_status s);
+
+/* ------------------------------------------------------------------------
+ * Completing the Ewald sum.  The short-range kernel computes the real-space
+ * term of non-excluded pairs inside rc (Sec. V.A); the paper runs the
+ * reciprocal part as a separate PME task on its own stream (Sec. IV).  With the
+ * self and exclusion terms below the four parts give the Ewald sum of a neutral
+ * periodic system with tin-foil boundaries:
+ *   E = E_real + E_recip + E_self + E_excl,  E_self = -f beta/sqrt(pi) sum q^2,
+ *   E_excl = -f sum_{excluded pairs} qi qj erf(beta r)/r,  f = 138.935458/eps_r.
+ * Virials use the convention of nb_forces (W = -1/2 sum r (x) F). */
+
+/* Smooth PME (cardinal B-spline charge assignment of order `order`, 3-D FFT on
+ * a K1 x K2 x K3 grid, influence function, inverse FFT, force gather). */
+typedef struct {
+    int n_atoms;
+    int grid[3];   /* K1, K2, K3 (each >= 2*order, <= 4096) */
+    int order;     /* B-spline order, 3..8 (4 is the usual choice) */
+    int reserved;  /* must be 0 */
+    double beta;   /* Ewald splitting parameter (nm^-1), > 0: the short-range part's */
+    double eps_r;  /* relative dielectric constant, > 0 */
+} nb_pme_params;
+
+/* Allocates the grids and the FFT plans (cuFFT) on the current device. */
+nb_status nb_pme_create(const nb_pme_params *params, nb_pme **out);
+void nb_pme_destroy(nb_pme *pme);
+
+/* Reciprocal-space energy, forces and virial at positions x_dev [N*3] (caller
+ * order, any periodic image) with charges q_dev [N] (device) in the
+ * rectangular box box_host [3].  Forces are ADDED to f_dev [N*3] (so that they
+ * can follow nb_forces on the same buffer); with NB_ENERGY e_dev[0] = E_recip
+ * (FP64, overwritten), with NB_VIRIAL vir_dev[9] (FP64, overwritten).  Weights,
+ * grid and FFTs are FP32 (fractional coordinates FP64), energy and virial sums
+ * FP64.  Asynchronous on `stream`; never allocates; calls on one nb_pme must
+ * not overlap on the GPU. */
+nb_status nb_pme_forces(nb_pme *pme, unsigned flags, const float *x_dev, const float *q_dev, const double *box_host,
+                        float *f_dev, double *e_dev, double *vir_dev, void *stream);
+
+/* Exclusion and self terms of a context built with NB_COULOMB_EWALD, at
+ * positions x_dev [N*3] (caller order), with its charges, exclusions, beta and
+ * the box of its last grid sort.  Forces are ADDED to f_dev [N*3]; with
+ * NB_ENERGY e_dev[2] = {E_excl, E_self} (overwritten); with NB_VIRIAL
+ * vir_dev[9] = W_excl (overwritten).  NB_ERR_INVALID_ARG for other Coulomb
+ * types, NB_ERR_NOT_READY before the first grid sort.  Asynchronous; never
+ * allocates. */
+nb_status nb_ewald_corrections(nb_ctx *ctx, unsigned flags, const float *x_dev, float *f_dev, double *e_dev,
+                               double *vir_dev, void *stream);
 
 /* ------------------------------------------------------------------------
  * Allocation-free evaluation of one small system.  The paper has no

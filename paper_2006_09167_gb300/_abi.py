@@ -35,7 +35,8 @@ EXPORTED = [
     "nb_prune_rolling", "nb_forces", "nb_forces_vjp", "nb_batch_create", "nb_batch_destroy",
     "nb_forces_batched", "nb_count_pairs", "nb_debug_export_pairs", "nb_debug_layout",
     "nb_get_stats", "nb_get_error", "nb_status_str", "nb_trace_enable", "nb_trace_read",
-    "nb_forces_small_noalloc", "nb_set_split",
+    "nb_forces_small_noalloc", "nb_set_split", "nb_pme_create", "nb_pme_destroy", "nb_pme_forces",
+    "nb_ewald_corrections",
 ]
 NB_NOALLOC_MAX_ATOMS = 16384
 NB_NOALLOC_MAX_TYPES = 8
@@ -52,6 +53,13 @@ class NbParams(ctypes.Structure):
         ("beta", ctypes.c_double), ("rc", ctypes.c_double), ("rlist", ctypes.c_double),
         ("r_in", ctypes.c_double), ("c6_host", ctypes.POINTER(ctypes.c_float)),
         ("c12_host", ctypes.POINTER(ctypes.c_float)),
+    ]
+
+
+class NbPmeParams(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("order", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("beta", ctypes.c_double), ("eps_r", ctypes.c_double),
     ]
 
 
@@ -109,11 +117,16 @@ def load(path: str = LIB_PATH):
     lib.nb_trace_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p]
     lib.nb_forces_small_noalloc.argtypes = [ctypes.POINTER(NbParams), vp, vp, vp, vp, vp,
                                             ctypes.POINTER(ctypes.c_double), ctypes.c_uint, vp, vp, vp, vp]
+    lib.nb_pme_create.argtypes = [ctypes.POINTER(NbPmeParams), ctypes.POINTER(vp)]
+    lib.nb_pme_destroy.argtypes = [vp]
+    lib.nb_pme_destroy.restype = None
+    lib.nb_pme_forces.argtypes = [vp, ctypes.c_uint, vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp, vp, vp]
+    lib.nb_ewald_corrections.argtypes = [vp, ctypes.c_uint, vp, vp, vp, vp, vp]
     lib.nb_status_str.argtypes = [ctypes.c_int]
     lib.nb_status_str.restype = ctypes.c_char_p
     for name in EXPORTED:
         fn = getattr(lib, name)
-        if name not in ("nb_destroy", "nb_batch_destroy", "nb_status_str") and fn.restype is not st:
+        if name not in ("nb_destroy", "nb_batch_destroy", "nb_pme_destroy", "nb_status_str") and fn.restype is not st:
             fn.restype = st
     _lib = lib
     return lib

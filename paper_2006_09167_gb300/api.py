@@ -186,6 +186,15 @@ class NbContext:
     def nb_get_error(self, stream=None) -> int:
         return int(self._lib.nb_get_error(self.handle, _stream(stream)))
 
+    def nb_ewald_corrections(self, flags: int, x: torch.Tensor, f: torch.Tensor, e: Optional[torch.Tensor] = None,
+                             vir: Optional[torch.Tensor] = None, stream=None):
+        """Exclusion and self terms of the Ewald sum; forces are added to f."""
+        ep = _dev(e, torch.float64, 2, "e") if (flags & NB_ENERGY) else None
+        vp = _dev(vir, torch.float64, 9, "vir") if (flags & NB_VIRIAL) else None
+        check(self._lib.nb_ewald_corrections(self.handle, ctypes.c_uint(flags), _dev(x, torch.float32, 3 * self.n, "x"),
+                                             _dev(f, torch.float32, 3 * self.n, "f"), ep, vp, _stream(stream)),
+              "nb_ewald_corrections")
+
     # ---- conveniences ---------------------------------------------------
     def build(self, x: torch.Tensor, box, rlist: Optional[float] = None, stream=None):
         """Grid sort plus outer-list search (with the first full prune at r_in)."""
@@ -200,6 +209,77 @@ class NbContext:
         flags = (NB_ENERGY if energy else 0) | (NB_VIRIAL if virial else 0)
         self.nb_forces(flags, x.contiguous(), f, e, w, stream)
         return f, e, (w.view(3, 3) if w is not None else None)
+
+
+def pme_grid(box, spacing: float = 0.12):
+    """PME grid sizes: per axis the smallest even number >= L/spacing whose prime
+    factors are 2, 3, 5 and 7 (sizes the FFT library handles fastest)."""
+    out = []
+    for L in np.asarray(box, np.float64):
+        k = max(int(math.ceil(float(L) / spacing)), 8)
+        while True:
+            m = k
+            for p in (2, 3, 5, 7):
+                while m % p == 0:
+                    m //= p
+            if m == 1 and k % 2 == 0:
+                break
+            k += 1
+        out.append(k)
+    return tuple(out)
+
+
+class NbPme:
+    """Wraps an nb_pme handle (smooth PME of the reciprocal-space Ewald term)."""
+
+    def __init__(self, n_atoms: int, beta: float, box=None, *, grid=None, spacing: float = 0.12, order: int = 4,
+                 eps_r: float = 1.0):
+        lib = _abi.load()
+        if grid is None:
+            if box is None:
+                raise ValueError("give the grid or a box to size it from")
+            grid = pme_grid(box, spacing)
+        p = _abi.NbPmeParams()
+        p.n_atoms = int(n_atoms)
+        for a in range(3):
+            p.grid[a] = int(grid[a])
+        p.order = int(order)
+        p.reserved = 0
+        p.beta = float(beta)
+        p.eps_r = float(eps_r)
+        h = ctypes.c_void_p()
+        check(lib.nb_pme_create(ctypes.byref(p), ctypes.byref(h)), "nb_pme_create")
+        self.handle = h
+        self._lib = lib
+        self.n = int(n_atoms)
+        self.grid = tuple(int(g) for g in grid)
+        self.order = int(order)
+
+    @classmethod
+    def from_system(cls, s, **kw) -> "NbPme":
+        return cls(s.n, s.beta, s.box, eps_r=s.eps_r, **kw)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.nb_pme_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def nb_pme_forces(self, flags: int, x: torch.Tensor, q: torch.Tensor, box, f: torch.Tensor,
+                      e: Optional[torch.Tensor] = None, vir: Optional[torch.Tensor] = None, stream=None):
+        """Reciprocal-space forces (added to f), energy e[0] and virial."""
+        b = (ctypes.c_double * 3)(*[float(v) for v in box])
+        ep = _dev(e, torch.float64, 1, "e") if (flags & NB_ENERGY) else None
+        vp = _dev(vir, torch.float64, 9, "vir") if (flags & NB_VIRIAL) else None
+        check(self._lib.nb_pme_forces(self.handle, ctypes.c_uint(flags), _dev(x, torch.float32, 3 * self.n, "x"),
+                                      _dev(q, torch.float32, self.n, "q"), b,
+                                      _dev(f, torch.float32, 3 * self.n, "f"), ep, vp, _stream(stream)),
+              "nb_pme_forces")
 
 
 class NbBatch:

@@ -67,7 +67,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
                     sys.stderr.write(p.stderr)
     if force or cmds or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call([nvcc, "-shared"] + ARCH + objs + ["-o", tmp])
+        subprocess.check_call([nvcc, "-shared"] + ARCH + objs + ["-lcufft", "-o", tmp])
         os.replace(tmp, LIB)
     return LIB
 

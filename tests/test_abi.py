@@ -129,3 +129,29 @@ def test_null_handles_are_rejected(lib):
     assert lib.nb_forces_batched(None, 0, None, None, None, None, None) == 1
     lib.nb_destroy(None)
     lib.nb_batch_destroy(None)
+
+
+@pytest.mark.parametrize("over", [dict(n_atoms=0), dict(order=2), dict(order=9), dict(grid=(6, 16, 16)),
+                                  dict(grid=(16, 16, 5000)), dict(beta=0.0), dict(beta=float("nan")),
+                                  dict(eps_r=0.0), dict(reserved=1)])
+def test_pme_create_rejects_bad_parameters_without_gpu(lib, over):
+    from paper_2006_09167_gb300 import _abi
+    p = _abi.NbPmeParams()
+    p.n_atoms, p.order, p.reserved, p.beta, p.eps_r = 10, 4, 0, 3.0, 1.0
+    for a in range(3):
+        p.grid[a] = 16
+    for k, v in over.items():
+        if k == "grid":
+            for a in range(3):
+                p.grid[a] = v[a]
+        else:
+            setattr(p, k, v)
+    h = ctypes.c_void_p()
+    assert lib.nb_pme_create(ctypes.byref(p), ctypes.byref(h)) == 1 and not h.value
+
+
+def test_pme_and_corrections_reject_null_handles(lib):
+    box = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    assert lib.nb_pme_forces(None, 0, None, None, box, None, None, None, None) == 1
+    assert lib.nb_ewald_corrections(None, 0, None, None, None, None, None) == 1
+    lib.nb_pme_destroy(None)
