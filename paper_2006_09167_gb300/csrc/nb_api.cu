@@ -220,7 +220,8 @@ nb_status nb_create(const nb_params *p, const float *q_host, const int32_t *type
     NB_TRY_ALLOC(dalloc(&c->diag, 4));
     NB_TRY_ALLOC(dalloc(&c->err, 1));
     NB_TRY_ALLOC(dalloc(&c->queue, 1));
-    NB_TRY_ALLOC(dalloc(&c->ewald_acc, 8));
+    NB_TRY_ALLOC(dalloc(&c->ewald_part, 8 * 1024));
+    NB_TRY_ALLOC(dalloc(&c->ewald_count, 1));
     NB_TRY_ALLOC(dalloc(&c->col_of, N));
     NB_TRY_ALLOC(dalloc(&c->rank_of, N));
     NB_TRY_ALLOC(dalloc(&c->colbuf, N));
@@ -237,7 +238,7 @@ nb_status nb_create(const nb_params *p, const float *q_host, const int32_t *type
     if (e == cudaSuccess) e = cudaMemcpy(c->lj, lj.data(), sizeof(float2) * T * T, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->lje, lje.data(), sizeof(float4) * T * T, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(c->ewald_acc, 0, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMemset(c->ewald_count, 0, sizeof(unsigned));
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -293,7 +294,8 @@ void nb_destroy(nb_ctx *c) {
     dfree(c->diag);
     dfree(c->err);
     dfree(c->queue);
-    dfree(c->ewald_acc);
+    dfree(c->ewald_part);
+    dfree(c->ewald_count);
     for (int k = 0; k < NB_TRACE_KINDS; k++) {
         for (auto e : c->ev_start[k]) cudaEventDestroy(e);
         for (auto e : c->ev_end[k]) cudaEventDestroy(e);

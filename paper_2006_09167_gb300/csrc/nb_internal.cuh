@@ -172,7 +172,8 @@ struct nb_ctx {
     long long *diag = nullptr;  // [4]
     int *err = nullptr;
     int *queue = nullptr;  // work-item counter of the persistent force kernel
-    double *ewald_acc = nullptr;  // [8] sums of the Ewald exclusion / self kernel (zero between calls)
+    double *ewald_part = nullptr;    // [1024*8] per-block rows of the Ewald exclusion / self kernel
+    unsigned *ewald_count = nullptr;  // its finished-block counter (zero between calls)
     int n_sm = 0;          // multiprocessors of the context's device
     long long n_launches = 0;
     // tracing: event pairs per traced kernel kind

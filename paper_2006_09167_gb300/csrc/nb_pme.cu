@@ -23,13 +23,14 @@
 using namespace nbk;
 
 struct nb_pme {
-    int n = 0, order = 0;
+    int n = 0, order = 0, n_sm = 1;
     int K[3] = {0, 0, 0};
     double beta = 0, eps_r = 1;
     float *grid = nullptr;       // [K1*K2*K3] real grid (charges, then the convolution)
     cufftComplex *cgrid = nullptr;  // [K1*K2*(K3/2+1)]
     float *bsp = nullptr;        // [K1+K2+K3] B-spline moduli |b(m)|^2 per axis
-    double *acc = nullptr;       // [7] energy and virial sums of the solve (without f)
+    double *part = nullptr;      // [kRows*8] per-block energy and virial rows of the solve (without f)
+    unsigned *count = nullptr;   // finished-block counter of the solve (zero between calls)
     cufftHandle fwd = 0, bwd = 0;
     bool have_fwd = false, have_bwd = false;
 };
@@ -37,6 +38,7 @@ struct nb_pme {
 namespace {
 
 constexpr int kPmeMaxOrder = 8;
+constexpr int kRows = 1024;  // grid cap of the reducing kernels (rows of partial sums)
 
 // M_n(w + j), j = 0..n-1 (cardinal B-spline of order n at the n grid offsets of
 // an atom with fractional part w), and d/dw of the same.  Built from the order-2
@@ -65,21 +67,32 @@ __device__ __forceinline__ void bspline_weights(float w, float (&th)[N], float (
 
 struct PmeGeom {
     int K[3];
-    double kl[3];  // K_a / L_a
+    float kl_hi[3], kl_lo[3];  // K_a / L_a as a float pair
 };
 
-// Base grid index in [0, K) and fractional part of coordinate x on one axis
-// (FP64).  False for a non-finite coordinate (the atom is then skipped).
-__device__ __forceinline__ bool frac_coord(float x, int K, double kl, int &fl, float &w) {
+// Base grid index in [0, K) and fractional part of coordinate x on one axis.
+// u = x K/L is formed as a float pair (the product split exactly by an FMA, K/L
+// itself a float pair), so the fractional part keeps ~1e-7 absolute accuracy
+// however large u is; the whole part is reduced modulo K in integers.  False
+// for a non-finite coordinate (the atom is then skipped).
+__device__ __forceinline__ bool frac_coord(float x, int K, float kl_hi, float kl_lo, int &fl, float &w) {
     if (!isfinite(x)) return false;
-    double u = (double)x * kl;
-    u -= (double)K * floor(u / (double)K);  // [0, K] up to rounding, which may leave -ulp or K
-    int f = (int)floor(u);
-    const double fr = u - (double)f;
+    const float u_hi = x * kl_hi;
+    const float u_lo = fmaf(x, kl_hi, -u_hi) + x * kl_lo;
+    float fh = floorf(u_hi);
+    float fr = (u_hi - fh) + u_lo;  // u_hi - fh is exact (|u_hi| < 2^24 for any sane box)
+    if (fr < 0.f) {
+        fr += 1.f;
+        fh -= 1.f;
+    } else if (fr >= 1.f) {
+        fr -= 1.f;
+        fh += 1.f;
+    }
+    if (!(fabsf(fh) < 1.6e7f)) return false;  // beyond exact integer range: treat as invalid input
+    int f = (int)fh % K;
     if (f < 0) f += K;
-    if (f >= K) f -= K;
     fl = min(max(f, 0), K - 1);
-    w = (float)fr;
+    w = fminf(fmaxf(fr, 0.f), 1.f);
     return true;
 }
 
@@ -99,7 +112,7 @@ __global__ void k_pme_spread(int n, const float *__restrict__ x, const float *__
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         float w = 0.f;
-        ok &= frac_coord(x[3 * i + a], g.K[a], g.kl[a], fl[a], w);
+        ok &= frac_coord(x[3 * i + a], g.K[a], g.kl_hi[a], g.kl_lo[a], fl[a], w);
         bspline_weights<ORDER>(w, th[a], dth);
     }
     if (!ok) return;
@@ -124,76 +137,135 @@ __global__ void k_pme_spread(int n, const float *__restrict__ x, const float *__
     }
 }
 
-// Influence function on the half spectrum: multiply each coefficient by
-// B(m) C(m) and sum the energy and virial terms (FP64; the Coulomb constant is
-// applied later).  Coefficients with 0 < m3 < K3/2 stand for two (m, -m).
-__global__ void k_pme_solve(cufftComplex *__restrict__ cg, int K1, int K2, int K3, float L0, float L1, float L2,
-                            float beta, const float *__restrict__ bsp, double *__restrict__ acc) {
-    const int K3h = K3 / 2 + 1;
-    const long long total = (long long)K1 * K2 * K3h;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double e = 0.0, w[6] = {0, 0, 0, 0, 0, 0};
-    if (idx < total) {
-        const int i2 = (int)(idx % K3h);
-        const int i1 = (int)((idx / K3h) % K2);
-        const int i0 = (int)(idx / ((long long)K3h * K2));
-        const float mx = (float)(i0 <= K1 / 2 ? i0 : i0 - K1) / L0;
-        const float my = (float)(i1 <= K2 / 2 ? i1 : i1 - K2) / L1;
-        const float mz = (float)i2 / L2;
-        const float m2 = mx * mx + my * my + mz * mz;
-        float eterm = 0.f;
-        if (idx != 0) {
-            const float pi = 3.14159265358979f;
-            const float V = L0 * L1 * L2;
-            eterm = expf(-pi * pi * m2 / (beta * beta)) / (pi * V * m2) * bsp[i0] * bsp[K1 + i1] * bsp[K1 + K2 + i2];
-            const cufftComplex d = cg[idx];
-            const float s2 = d.x * d.x + d.y * d.y;
-            const float wgt = (i2 == 0 || (K3 % 2 == 0 && i2 == K3 / 2)) ? 1.f : 2.f;
-            const double ek = 0.5 * (double)wgt * (double)eterm * (double)s2;
-            e = ek;
-            const double g2 = 2.0 * (1.0 + (double)(pi * pi * m2 / (beta * beta))) / (double)m2;
-            const double m[3] = {mx, my, mz};
-            // xx, yy, zz, xy, xz, yz of -1/2 e (delta - g2 m m)
-            w[0] = -0.5 * ek * (1.0 - g2 * m[0] * m[0]);
-            w[1] = -0.5 * ek * (1.0 - g2 * m[1] * m[1]);
-            w[2] = -0.5 * ek * (1.0 - g2 * m[2] * m[2]);
-            w[3] = 0.5 * ek * g2 * m[0] * m[1];
-            w[4] = 0.5 * ek * g2 * m[0] * m[2];
-            w[5] = 0.5 * ek * g2 * m[1] * m[2];
-        }
-        cufftComplex d = cg[idx];
-        d.x *= eterm;
-        d.y *= eterm;
-        cg[idx] = d;
-    }
-    // block reduction of the 7 sums, then one atomic per sum per block
-    __shared__ double s_red[7][32];
+// Block sum of NV per-thread values: value k is taken from d[] and summed in FP64
+// throughout if bit k of D64 is set, else from a[] and summed in FP32 within a
+// warp and FP64 across warps.  The block totals land in s_tot[0..NV) (shared
+// memory), valid after the call in every thread.
+template <int NV, unsigned D64>
+__device__ void block_sum(const float (&a)[NV], const double (&d)[NV], double *s_tot) {
+    __shared__ double s_red[8][32];
     const unsigned full = 0xffffffffu;
-    double v[7] = {e, w[0], w[1], w[2], w[3], w[4], w[5]};
-#pragma unroll
-    for (int k = 0; k < 7; k++)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(full, v[k], o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int k = 0; k < 7; k++) s_red[k][wid] = v[k];
-    __syncthreads();
-    if (threadIdx.x < 7) {
-        double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += s_red[threadIdx.x][k];
-        atomicAdd(&acc[threadIdx.x], s);
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double v;
+        if (!((D64 >> k) & 1u)) {
+            float x = a[k];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(full, x, o);
+            v = (double)x;
+        } else {
+            v = d[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+        }
+        if (lane == 0) s_red[k][wid] = v;
     }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_red[threadIdx.x][w];
+        s_tot[threadIdx.x] = t;
+    }
+    __syncthreads();
 }
 
-// Energy and virial out (times the Coulomb constant), accumulators zeroed.
-__global__ void k_pme_finish(double *acc, double fc, double *e, double *vir) {
-    if (threadIdx.x != 0) return;
-    if (e) e[0] = fc * acc[0];
-    if (vir) {
-        const double xx = acc[1], yy = acc[2], zz = acc[3], xy = acc[4], xz = acc[5], yz = acc[6];
-        const double W[9] = {xx, xy, xz, xy, yy, yz, xz, yz, zz};
-        for (int k = 0; k < 9; k++) vir[k] = fc * W[k];
+// End of a two-stage reduction without a second launch: every block writes its
+// row of NV totals (FP64); the last block to finish (a device counter, which that
+// block resets) folds all rows in a fixed order and writes the outputs times the
+// Coulomb constant fc.  Row layout: NE energies, then xx, yy, zz, xy, xz, yz.
+// No block waits for another.
+template <int NE>
+__device__ void rows_out(const double *s_tot, double *__restrict__ part, unsigned *__restrict__ count, double fc,
+                         double *e, double *vir) {
+    constexpr int NV = NE + 6;
+    __shared__ bool s_last;
+    if (threadIdx.x < NV) part[(size_t)blockIdx.x * 8 + threadIdx.x] = s_tot[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the whole block folds the rows: strided partial sums, then a block sum
+    double t[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) t[k] = 0.0;
+    for (unsigned r = threadIdx.x; r < gridDim.x; r += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; k++) t[k] += __ldcg(part + (size_t)r * 8 + k);
+    __shared__ double s_fold[NV][32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(full, t[k], o);
+        if (lane == 0) s_fold[k][wid] = t[k];
     }
-    for (int k = 0; k < 7; k++) acc[k] = 0.0;
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += s_fold[threadIdx.x][w];
+        const int k = threadIdx.x;
+        if (k < NE) {
+            if (e) e[k] = fc * tot;
+        } else if (vir) {
+            const int c = k - NE;  // xx, yy, zz, xy, xz, yz -> row-major 3x3 slots
+            const int ia = c < 3 ? 4 * c : (c == 3 ? 1 : (c == 4 ? 2 : 5));
+            const int ib = c < 3 ? 4 * c : (c == 3 ? 3 : (c == 4 ? 6 : 7));
+            vir[ia] = fc * tot;
+            vir[ib] = fc * tot;
+        }
+    }
+    if (threadIdx.x == 0) *count = 0u;
+}
+
+// Influence function on the half spectrum: multiply each coefficient by
+// B(m) C(m) and sum the energy and virial terms (the Coulomb constant is applied
+// at the end).  Coefficients with 0 < m3 < K3/2 stand for two (m, -m).  Each warp
+// walks whole rows (i0, i1) of the half spectrum, lanes along i3; a capped grid.
+__global__ void k_pme_solve(cufftComplex *__restrict__ cg, int K1, int K2, int K3, float L0, float L1, float L2,
+                            float beta, const float *__restrict__ bsp, double *__restrict__ part,
+                            unsigned *__restrict__ count, double fc, double *e, double *vir) {
+    const int K3h = K3 / 2 + 1;
+    const float pi = 3.14159265358979f;
+    const float V = L0 * L1 * L2;
+    const float pb2 = pi * pi / (beta * beta);
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+    float a[7] = {0, 0, 0, 0, 0, 0, 0};  // E, xx, yy, zz, xy, xz, yz of -1/2 e (delta - g2 m m)
+    for (int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); r < K1 * K2; r += warps) {
+        const int i0 = r / K2, i1 = r - i0 * K2;
+        const float mx = (float)(i0 <= K1 / 2 ? i0 : i0 - K1) / L0;
+        const float my = (float)(i1 <= K2 / 2 ? i1 : i1 - K2) / L1;
+        const float bxy = bsp[i0] * bsp[K1 + i1];
+        cufftComplex *row = cg + (size_t)r * K3h;
+        for (int i2 = lane; i2 < K3h; i2 += 32) {
+            const float mz = (float)i2 / L2;
+            const float m2 = mx * mx + my * my + mz * mz;
+            cufftComplex d = row[i2];
+            float eterm = 0.f;
+            if (r != 0 || i2 != 0) {
+                eterm = __expf(-pb2 * m2) / (pi * V * m2) * bxy * bsp[K1 + K2 + i2];
+                const float s2 = d.x * d.x + d.y * d.y;
+                const float wgt = (i2 == 0 || (K3 % 2 == 0 && i2 == K3 / 2)) ? 0.5f : 1.f;
+                const float ek = wgt * eterm * s2;
+                const float h = ek * (1.f + pb2 * m2) / m2;  // 1/2 ek g2
+                a[0] += ek;
+                a[1] += fmaf(h * mx, mx, -0.5f * ek);
+                a[2] += fmaf(h * my, my, -0.5f * ek);
+                a[3] += fmaf(h * mz, mz, -0.5f * ek);
+                a[4] += h * mx * my;
+                a[5] += h * mx * mz;
+                a[6] += h * my * mz;
+            }
+            d.x *= eterm;
+            d.y *= eterm;
+            row[i2] = d;
+        }
+    }
+    __shared__ double s_tot[8];
+    const double dz[7] = {0, 0, 0, 0, 0, 0, 0};
+    block_sum<7, 0u>(a, dz, s_tot);
+    rows_out<1>(s_tot, part, count, fc, e, vir);
 }
 
 // Force gather: one thread per atom, F_i = -f q_i sum_k grad(weights) conv(k).
@@ -210,7 +282,7 @@ __global__ void k_pme_gather(int n, const float *__restrict__ x, const float *__
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         float w = 0.f;
-        ok &= frac_coord(x[3 * i + a], g.K[a], g.kl[a], fl[a], w);
+        ok &= frac_coord(x[3 * i + a], g.K[a], g.kl_hi[a], g.kl_lo[a], fl[a], w);
         bspline_weights<ORDER>(w, th[a], dth[a]);
     }
     if (!ok) return;
@@ -239,9 +311,9 @@ __global__ void k_pme_gather(int n, const float *__restrict__ x, const float *__
         }
     }
     const float c = -fcoul * qi;
-    f[3 * i] += c * fx * (float)g.kl[0];
-    f[3 * i + 1] += c * fy * (float)g.kl[1];
-    f[3 * i + 2] += c * fz * (float)g.kl[2];
+    f[3 * i] += c * fx * g.kl_hi[0];
+    f[3 * i + 1] += c * fy * g.kl_hi[1];
+    f[3 * i + 2] += c * fz * g.kl_hi[2];
 }
 
 template <int ORDER>
@@ -301,17 +373,20 @@ std::vector<double> bspline_moduli(int K, int order) {
 // CSR): V = -f qi qj erf(beta r)/r per excluded pair, whose force is
 // -f qi qj beta^3 H(beta r) r_vec with the same H as the force kernel (no
 // cancellation at small r); energies and virial of each pair are taken by the
-// lower index, forces by both atoms (no atomics).  Self: -f beta/sqrt(pi) q^2.
+// lower index, forces by both atoms (no atomics).  Self: -f beta/sqrt(pi) q^2
+// (summed in FP64).  A capped grid walks the atoms; partial sums {E_excl, E_self,
+// xx, yy, zz, xy, xz, yz} are folded by the last block.
 __global__ void k_ewald_corr(int n, const float *__restrict__ x, const float *__restrict__ q,
                              const int *__restrict__ off, const int *__restrict__ idx, float Lx, float Ly, float Lz,
                              float beta, double beta_d, float ew_s, float fcoul, float *__restrict__ f,
-                             double *__restrict__ acc) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // E_excl, E_self, xx, yy, zz, xy, xz, yz (without f)
-    if (i < n) {
+                             double *__restrict__ part, unsigned *__restrict__ count, double fc, double *e,
+                             double *vir) {
+    float a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const float b3 = beta * beta * beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float qi = q[i];
         const float xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
-        const float b3 = beta * beta * beta;
         float fx = 0.f, fy = 0.f, fz = 0.f;
         for (int p = off[i]; p < off[i + 1]; p++) {
             const int j = idx[p];
@@ -334,51 +409,24 @@ __global__ void k_ewald_corr(int n, const float *__restrict__ x, const float *__
             fy = fmaf(phi, dy, fy);
             fz = fmaf(phi, dz, fz);
             if (j > i) {
-                const double vij = r2 > 0.f ? -(double)qq * (double)erff(z) / (double)r
-                                            : -(double)qq * 1.1283791670955126 * (double)beta;
-                v[0] += vij;
-                const double pd = (double)phi;
-                v[2] += -0.5 * pd * dx * dx;
-                v[3] += -0.5 * pd * dy * dy;
-                v[4] += -0.5 * pd * dz * dz;
-                v[5] += -0.5 * pd * dx * dy;
-                v[6] += -0.5 * pd * dx * dz;
-                v[7] += -0.5 * pd * dy * dz;
+                a[0] += r2 > 0.f ? -qq * (erff(z) / r) : -qq * 1.1283791670955126f * beta;
+                const float hp = -0.5f * phi;
+                a[2] += hp * dx * dx;
+                a[3] += hp * dy * dy;
+                a[4] += hp * dz * dz;
+                a[5] += hp * dx * dy;
+                a[6] += hp * dx * dz;
+                a[7] += hp * dy * dz;
             }
         }
-        v[1] = -beta_d * 0.5641895835477563 * (double)qi * (double)qi;
+        d[1] += -beta_d * 0.5641895835477563 * (double)qi * (double)qi;
         f[3 * i] += fcoul * fx;
         f[3 * i + 1] += fcoul * fy;
         f[3 * i + 2] += fcoul * fz;
     }
-    __shared__ double s_red[8][32];
-    const unsigned full = 0xffffffffu;
-#pragma unroll
-    for (int k = 0; k < 8; k++)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(full, v[k], o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int k = 0; k < 8; k++) s_red[k][wid] = v[k];
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += s_red[threadIdx.x][k];
-        atomicAdd(&acc[threadIdx.x], s);
-    }
-}
-
-__global__ void k_ewald_corr_finish(double *acc, double fc, double *e, double *vir) {
-    if (threadIdx.x != 0) return;
-    if (e) {
-        e[0] = fc * acc[0];
-        e[1] = fc * acc[1];
-    }
-    if (vir) {
-        const double xx = acc[2], yy = acc[3], zz = acc[4], xy = acc[5], xz = acc[6], yz = acc[7];
-        const double W[9] = {xx, xy, xz, xy, yy, yz, xz, yz, zz};
-        for (int k = 0; k < 9; k++) vir[k] = fc * W[k];
-    }
-    for (int k = 0; k < 8; k++) acc[k] = 0.0;
+    __shared__ double s_tot[8];
+    block_sum<8, 2u>(a, d, s_tot);
+    rows_out<2>(s_tot, part, count, fc, e, vir);
 }
 
 bool box_ok(const double *box) {
@@ -398,6 +446,7 @@ nb_status nb_pme_create(const nb_pme_params *pp, nb_pme **out) {
     if (pp->n_atoms < 1 || pp->order < 3 || pp->order > kPmeMaxOrder || pp->reserved != 0) return NB_ERR_INVALID_ARG;
     for (int a = 0; a < 3; a++)
         if (pp->grid[a] < 2 * pp->order || pp->grid[a] > 4096) return NB_ERR_INVALID_ARG;
+    if ((long long)pp->grid[0] * pp->grid[1] * (pp->grid[2] / 2 + 1) >= (1ll << 31)) return NB_ERR_INVALID_ARG;
     if (!(pp->beta > 0.0) || !isfinite(pp->beta) || !(pp->eps_r > 0.0) || !isfinite(pp->eps_r))
         return NB_ERR_INVALID_ARG;
     nb_pme *p = new (std::nothrow) nb_pme;
@@ -407,13 +456,18 @@ nb_status nb_pme_create(const nb_pme_params *pp, nb_pme **out) {
     for (int a = 0; a < 3; a++) p->K[a] = pp->grid[a];
     p->beta = pp->beta;
     p->eps_r = pp->eps_r;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || p->n_sm < 1)
+        p->n_sm = 1;
     const size_t nr = (size_t)p->K[0] * p->K[1] * p->K[2];
     const size_t nc = (size_t)p->K[0] * p->K[1] * (p->K[2] / 2 + 1);
     cudaError_t e = cudaMalloc((void **)&p->grid, sizeof(float) * nr);
     if (e == cudaSuccess) e = cudaMalloc((void **)&p->cgrid, sizeof(cufftComplex) * nc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&p->bsp, sizeof(float) * (p->K[0] + p->K[1] + p->K[2]));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&p->acc, sizeof(double) * 8);
-    if (e == cudaSuccess) e = cudaMemset(p->acc, 0, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p->part, sizeof(double) * 8 * kRows);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p->count, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(p->count, 0, sizeof(unsigned));
     if (e == cudaSuccess) {
         std::vector<float> b;
         for (int a = 0; a < 3; a++) {
@@ -447,7 +501,8 @@ void nb_pme_destroy(nb_pme *p) {
     cudaFree(p->grid);
     cudaFree(p->cgrid);
     cudaFree(p->bsp);
-    cudaFree(p->acc);
+    cudaFree(p->part);
+    cudaFree(p->count);
     delete p;
 }
 
@@ -460,8 +515,10 @@ nb_status nb_pme_forces(nb_pme *p, unsigned flags, const float *x_dev, const flo
     cudaStream_t st = (cudaStream_t)stream;
     PmeGeom g;
     for (int a = 0; a < 3; a++) {
+        const double kl = (double)p->K[a] / box_host[a];
         g.K[a] = p->K[a];
-        g.kl[a] = (double)p->K[a] / box_host[a];
+        g.kl_hi[a] = (float)kl;
+        g.kl_lo[a] = (float)(kl - (double)g.kl_hi[a]);
     }
     const size_t nr = (size_t)p->K[0] * p->K[1] * p->K[2];
     const size_t nc = (size_t)p->K[0] * p->K[1] * (p->K[2] / 2 + 1);
@@ -471,12 +528,12 @@ nb_status nb_pme_forces(nb_pme *p, unsigned flags, const float *x_dev, const flo
     NB_CUDA_TRY(cudaGetLastError());
     if (cufftSetStream(p->fwd, st) != CUFFT_SUCCESS || cufftExecR2C(p->fwd, p->grid, p->cgrid) != CUFFT_SUCCESS)
         return NB_ERR_CUDA;
-    k_pme_solve<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(p->cgrid, p->K[0], p->K[1], p->K[2], (float)box_host[0],
-                                                            (float)box_host[1], (float)box_host[2], (float)p->beta,
-                                                            p->bsp, p->acc);
-    NB_CUDA_TRY(cudaGetLastError());
-    k_pme_finish<<<1, 32, 0, st>>>(p->acc, 138.935458 / p->eps_r, (flags & NB_ENERGY) ? e_dev : nullptr,
-                                   (flags & NB_VIRIAL) ? vir_dev : nullptr);
+    // one warp per spectrum row (K1*K2 rows), at most kRows blocks of 8 warps
+    const int sblocks = std::min((p->K[0] * p->K[1] + 7) / 8, std::min(2 * p->n_sm, kRows));
+    k_pme_solve<<<sblocks, 256, 0, st>>>(p->cgrid, p->K[0], p->K[1], p->K[2], (float)box_host[0], (float)box_host[1],
+                                         (float)box_host[2], (float)p->beta, p->bsp, p->part, p->count,
+                                         138.935458 / p->eps_r, (flags & NB_ENERGY) ? e_dev : nullptr,
+                                         (flags & NB_VIRIAL) ? vir_dev : nullptr);
     NB_CUDA_TRY(cudaGetLastError());
     if (cufftSetStream(p->bwd, st) != CUFFT_SUCCESS || cufftExecC2R(p->bwd, p->cgrid, p->grid) != CUFFT_SUCCESS)
         return NB_ERR_CUDA;
@@ -495,13 +552,13 @@ nb_status nb_ewald_corrections(nb_ctx *c, unsigned flags, const float *x_dev, fl
     if (!c->have_grid) return NB_ERR_NOT_READY;  // the box comes from the last grid sort
     cudaStream_t st = (cudaStream_t)stream;
     const float ew_s = (float)(c->beta * c->beta / (NB_EW_ZMAX_D * NB_EW_ZMAX_D));
-    c->n_launches += 2;
-    k_ewald_corr<<<(c->N + 127) / 128, 128, 0, st>>>(c->N, x_dev, c->q, c->excl_off, c->excl_idx, (float)c->box[0],
-                                                     (float)c->box[1], (float)c->box[2], (float)c->beta, c->beta, ew_s,
-                                                     (float)(138.935458 / c->eps_r), f_dev, c->ewald_acc);
-    NB_CUDA_TRY(cudaGetLastError());
-    k_ewald_corr_finish<<<1, 32, 0, st>>>(c->ewald_acc, 138.935458 / c->eps_r, (flags & NB_ENERGY) ? e_dev : nullptr,
-                                          (flags & NB_VIRIAL) ? vir_dev : nullptr);
+    c->n_launches += 1;
+    const int blocks = std::min((c->N + 255) / 256, std::min(2 * std::max(c->n_sm, 1), kRows));
+    k_ewald_corr<<<blocks, 256, 0, st>>>(c->N, x_dev, c->q, c->excl_off, c->excl_idx, (float)c->box[0],
+                                         (float)c->box[1], (float)c->box[2], (float)c->beta, c->beta, ew_s,
+                                         (float)(138.935458 / c->eps_r), f_dev, c->ewald_part, c->ewald_count,
+                                         138.935458 / c->eps_r, (flags & NB_ENERGY) ? e_dev : nullptr,
+                                         (flags & NB_VIRIAL) ? vir_dev : nullptr);
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
 }
