@@ -55,7 +55,7 @@ FLOPS_PER_PAIR = {
 # DRAM bytes (read + write) of one k_forces<Ewald, energy, virial> launch on the
 # 96k box from the ncu capture summarised in profiles/k_forces_spce_water_96k.md;
 # set to None whenever the force kernel changes until it is captured again.
-FORCE_KERNEL_DRAM_BYTES = 7618816
+FORCE_KERNEL_DRAM_BYTES = None
 
 
 def rank_env():
@@ -540,11 +540,27 @@ def main_reference(args):
 
 
 def main_profile(args):
-    """A short, fixed launch sequence for profilers: one build, then force evaluations."""
+    """A short, fixed launch sequence for profilers: one build, then force evaluations
+    (--profile-case forces) or PME + Ewald-correction calls (--profile-case pme)."""
     import torch
     from paper_2006_09167_gb300 import api, synth
     s = synth.water_96k()
     ctx = api.NbContext.from_system(s)
+    if args.profile_case == "pme":
+        x = torch.tensor(s.x, device="cuda")
+        q = torch.tensor(s.q, device="cuda")
+        ctx.build(x, s.box)
+        pme = api.NbPme.from_system(s, spacing=0.12, order=4)
+        f = torch.zeros((s.n, 3), dtype=torch.float32, device="cuda")
+        e1 = torch.empty(1, dtype=torch.float64, device="cuda")
+        e2 = torch.empty(2, dtype=torch.float64, device="cuda")
+        w = torch.empty(9, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            pme.nb_pme_forces(api.NB_ENERGY | api.NB_VIRIAL, x, q, s.box, f, e1, w)
+            ctx.nb_ewald_corrections(api.NB_ENERGY | api.NB_VIRIAL, x, f, e2, w)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "spce_water_96k_pme_order4_grid84", "calls": args.warmup + args.steps}))
+        return
     if args.split:
         ctx.nb_set_split(args.split)
     x = torch.tensor(s.x, device="cuda")
@@ -571,6 +587,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true",
                     help="profiling target: warmup + steps force evaluations (energy+virial) of the 96k box only")
+    ap.add_argument("--profile-case", choices=["forces", "pme"], default="forces",
+                    help="with --profile: the launch sequence to run")
     ap.add_argument("--split", type=int, default=0,
                     help="with --profile: the work-item split to build with (default: the library's)")
     args = ap.parse_args()

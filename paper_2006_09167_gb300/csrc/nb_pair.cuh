@@ -56,6 +56,62 @@ __device__ __forceinline__ float ew_x(float z) {
     return __fdividef(p, q);
 }
 
+// Packed FP32 (sm_100 and later): one FFMA2 / FMUL2 / FADD2 instruction performs
+// the operation on both components of a float2, each rounded exactly as the
+// scalar operation.  The force kernel evaluates two pairs per lane, so their
+// arithmetic runs on pairs of values and takes half the issue slots.
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __fadd2_rn(a, pneg(b)); }
+
+// ew_h, ew_expm and ew_x on two values (the same operations per component)
+__device__ __forceinline__ float2 ew_h2(float2 s) {
+    float2 p = pfma(p2(NB_EW_HP6), s, p2(NB_EW_HP5));
+    p = pfma(p, s, p2(NB_EW_HP4));
+    p = pfma(p, s, p2(NB_EW_HP3));
+    p = pfma(p, s, p2(NB_EW_HP2));
+    p = pfma(p, s, p2(NB_EW_HP1));
+    p = pfma(p, s, p2(NB_EW_HP0));
+    float2 q = pfma(p2(NB_EW_HQ5), s, p2(NB_EW_HQ4));
+    q = pfma(q, s, p2(NB_EW_HQ3));
+    q = pfma(q, s, p2(NB_EW_HQ2));
+    q = pfma(q, s, p2(NB_EW_HQ1));
+    q = pfma(q, s, p2(1.0f));
+    return make_float2(__fdividef(p.x, q.x), __fdividef(p.y, q.y));
+}
+
+__device__ __forceinline__ float2 ew_expm2(float2 x) {
+    const float2 nl = pmul(x, p2(NB_EXP_LOG2E));
+    const float2 n = make_float2(rintf(nl.x), rintf(nl.y));
+    float2 u = pfma(pneg(n), p2(NB_EXP_LN2_HI), x);
+    u = pfma(pneg(n), p2(NB_EXP_LN2_LO), u);
+    const float2 w = pneg(u);
+    float2 q = pfma(p2(NB_EXP_C7), w, p2(NB_EXP_C6));
+    q = pfma(q, w, p2(NB_EXP_C5));
+    q = pfma(q, w, p2(NB_EXP_C4));
+    q = pfma(q, w, p2(NB_EXP_C3));
+    q = pfma(q, w, p2(NB_EXP_C2));
+    q = pfma(q, w, p2(NB_EXP_C1));
+    const float2 p = pfma(q, w, p2(1.0f));
+    return pmul(p, make_float2(__int_as_float((127 - (int)n.x) << 23), __int_as_float((127 - (int)n.y) << 23)));
+}
+
+__device__ __forceinline__ float2 ew_x2(float2 z) {
+    const float2 t = pmul(z, p2(1.0f / NB_EW_ZMAX));
+    float2 p = pfma(p2(NB_EW_XP4), t, p2(NB_EW_XP3));
+    p = pfma(p, t, p2(NB_EW_XP2));
+    p = pfma(p, t, p2(NB_EW_XP1));
+    p = pfma(p, t, p2(NB_EW_XP0));
+    float2 q = pfma(p2(NB_EW_XQ4), t, p2(NB_EW_XQ3));
+    q = pfma(q, t, p2(NB_EW_XQ2));
+    q = pfma(q, t, p2(NB_EW_XQ1));
+    q = pfma(q, t, p2(1.0f));
+    return make_float2(__fdividef(p.x, q.x), __fdividef(p.y, q.y));
+}
+
 // Periodic shift of a work item split between the two sides of each pair so
 // that every shifted coordinate stays exact.  For shift s (per axis) the pair
 // vector is x_i - x_j + s L.  On an axis with s = -1 the i-atoms lie near the
@@ -174,6 +230,68 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
     return phi;
 }
 
+// Two pairs (i, j0) and (i, j1) at once: pair_phi's operations, in the same
+// order, on float2 values (component 0: j0, component 1: j1).  Energies are added
+// per component to elj / ec.
+template <int COUL, bool EN>
+__device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__restrict__ ljt,
+                                            const float4 *__restrict__ lje, float2 dx, float2 dy, float2 dz, float qi,
+                                            float2 qj, int tp0, int tp1, bool b0, bool b1, float2 &elj, float2 &ec) {
+    float2 r2 = pfma(dz, dz, pfma(dy, dy, pmul(dx, dx)));
+    const bool in0 = b0 && (r2.x < v.rc2), in1 = b1 && (r2.y < v.rc2);
+    r2.x = in0 ? r2.x : v.rc2;
+    r2.y = in1 ? r2.y : v.rc2;
+    float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (EN) {  // rsqrt_refine
+        const float2 e = pfma(pneg(pmul(r2, rinv)), rinv, p2(1.0f));
+        rinv = pfma(pmul(p2(0.5f), rinv), e, rinv);
+    }
+    const float2 rinv2 = pmul(rinv, rinv);
+    const float2 rinv6 = pmul(pmul(rinv2, rinv2), rinv2);
+    const float2 la = ljt[tp0], lb = ljt[tp1];  // (6 C6, 12 C12)
+    const float2 flj = pmul(rinv6, pfma(make_float2(la.y, lb.y), rinv6, make_float2(-la.x, -lb.x)));
+    const float2 qq = pmul(p2(qi), qj);
+    float2 fc = p2(0.f), erfcz = p2(0.f);
+    if (COUL == NB_COULOMB_RF) {
+        fc = pmul(qq, pfma(rinv, rinv2, p2(-2.0f * v.k_rf)));
+    } else if (COUL == NB_COULOMB_EWALD) {
+        if (EN) {
+            const float2 ex = ew_expm2(pmul(r2, p2(v.ew_beta2)));
+            erfcz = pmul(ex, ew_x2(pmul(p2(v.ew_beta), pmul(r2, rinv))));
+            fc = pmul(pmul(qq, rinv2), pfma(erfcz, rinv, pmul(p2(v.ew_2bsp), ex)));
+        } else {
+            fc = pmul(qq, pfma(rinv, rinv2, pmul(p2(-v.ew_beta3), ew_h2(pmul(r2, p2(v.ew_s))))));
+        }
+    }
+    if (EN) fc = pmul(fc, p2(v.coul_f));
+    float2 phi = pfma(flj, rinv2, fc);
+    phi.x = in0 ? phi.x : 0.f;
+    phi.y = in1 ? phi.y : 0.f;
+    if (EN) {
+        const float4 ea = lje[tp0], eb = lje[tp1];  // (C6, C12, C12/rc^12 - C6/rc^6, -)
+        float2 vlj = pfma(rinv6, pfma(make_float2(ea.y, eb.y), rinv6, make_float2(-ea.x, -eb.x)),
+                          make_float2(-ea.z, -eb.z));
+        float2 vc = p2(0.f);
+        if (COUL == NB_COULOMB_RF) {
+            const float2 t_hi = pmul(rinv, rinv);
+            const float2 t_lo = pfma(rinv, rinv, pneg(t_hi));
+            const float2 e = psub(pfma(pneg(r2), t_hi, p2(1.0f)), pmul(r2, t_lo));
+            const float2 rlo = pmul(pmul(p2(0.5f), rinv), e);
+            vc = padd(psub(rinv, p2(v.c_rf)), padd(pfma(p2(v.k_rf), r2, p2(-v.c_rf_lo)), rlo));
+        } else if (COUL == NB_COULOMB_EWALD) {
+            vc = pfma(erfcz, rinv, p2(-v.ew_shift));
+        }
+        float2 qv = pmul(qq, vc);
+        vlj.x = in0 ? vlj.x : 0.f;
+        vlj.y = in1 ? vlj.y : 0.f;
+        qv.x = in0 ? qv.x : 0.f;
+        qv.y = in1 ? qv.y : 0.f;
+        elj = padd(elj, vlj);
+        ec = padd(ec, qv);
+    }
+    return phi;
+}
+
 // Evaluate work item w (nj > 0 inner entries) with one warp.  s_xi / s_ti are
 // this warp's 64-entry staging arrays and s_fi its i-force accumulators
 // ([8 clusters][3][32 lanes] floats, conflict-free); ljt / lje the pair tables
@@ -215,9 +333,13 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             xj1 = shift_j(xj1, sh);
         }
         const int tj0 = v.type[cj * NB_CL + tj], tj1 = v.type[cj * NB_CL + tj + 4];
-        float f0x = 0.f, f0y = 0.f, f0z = 0.f, f1x = 0.f, f1y = 0.f, f1z = 0.f;
+        // the lane's two j-atoms as packed pairs (component 0: tj, component 1: tj + 4)
+        const float2 jx = make_float2(xj0.x, xj1.x), jy = make_float2(xj0.y, xj1.y);
+        const float2 jz = make_float2(xj0.z, xj1.z), jq = make_float2(xj0.w, xj1.w);
+        float2 fjx = p2(0.f), fjy = p2(0.f), fjz = p2(0.f);  // j-forces of the two atoms
+        float2 elj2 = p2(0.f), ec2 = p2(0.f);
         float elj_e = 0.f, ec_e = 0.f;
-        // i-clusters that interact with both j-halves: two independent pairs per lane
+        // i-clusters that interact with both j-halves: two pairs per lane, packed
         int both = lo & hi;
 #pragma unroll 1
         while (both) {
@@ -231,22 +353,17 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             }
             const float4 xi = s_xi[k * NB_CL + ti];
             const int tio = s_ti[k * NB_CL + ti];
-            const float3 d0 = make_float3(xi.x - xj0.x, xi.y - xj0.y, xi.z - xj0.z);
-            const float3 d1 = make_float3(xi.x - xj1.x, xi.y - xj1.y, xi.z - xj1.z);
-            const float p0 = pair_phi<COUL, EN>(v, ljt, lje, d0, xi.w, xj0.w, tio + tj0, b0, elj_e, ec_e);
-            const float p1 = pair_phi<COUL, EN>(v, ljt, lje, d1, xi.w, xj1.w, tio + tj1, b1, elj_e, ec_e);
-            const float ax = p0 * d0.x, ay = p0 * d0.y, az = p0 * d0.z;
-            const float bx = p1 * d1.x, by = p1 * d1.y, bz = p1 * d1.z;
+            const float2 dx = psub(p2(xi.x), jx), dy = psub(p2(xi.y), jy), dz = psub(p2(xi.z), jz);
+            const float2 p = pair_phi2<COUL, EN>(v, ljt, lje, dx, dy, dz, xi.w, jq, tio + tj0, tio + tj1, b0, b1,
+                                                 elj2, ec2);
+            const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
             float *fk = s_fi + k * 96 + lane;
-            fk[0] += ax + bx;
-            fk[32] += ay + by;
-            fk[64] += az + bz;
-            f0x -= ax;
-            f0y -= ay;
-            f0z -= az;
-            f1x -= bx;
-            f1y -= by;
-            f1z -= bz;
+            fk[0] += ax.x + ax.y;
+            fk[32] += ay.x + ay.y;
+            fk[64] += az.x + az.y;
+            fjx = psub(fjx, ax);
+            fjy = psub(fjy, ay);
+            fjz = psub(fjz, az);
         }
         // i-clusters that the prune kept for one j-half only: one pair per lane
         int one = lo ^ hi;
@@ -271,15 +388,20 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             fk[32] += ay;
             fk[64] += az;
             if (upper) {
-                f1x -= ax;
-                f1y -= ay;
-                f1z -= az;
+                fjx.y -= ax;
+                fjy.y -= ay;
+                fjz.y -= az;
             } else {
-                f0x -= ax;
-                f0y -= ay;
-                f0z -= az;
+                fjx.x -= ax;
+                fjy.x -= ay;
+                fjz.x -= az;
             }
         }
+        if (EN) {
+            elj_e += elj2.x + elj2.y;
+            ec_e += ec2.x + ec2.y;
+        }
+        const float f0x = fjx.x, f0y = fjy.x, f0z = fjz.x, f1x = fjx.y, f1y = fjy.y, f1z = fjz.y;
         if (EN) {
             elj.add(elj_e);
             ec.add(ec_e);
