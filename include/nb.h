@@ -159,7 +159,9 @@ nb_status nb_prune_rolling(nb_ctx *ctx, float r_in, int part, int n_parts, void 
  * accumulation are FP32; energies and virial are reduced in FP64.
  * Asynchronous; never allocates; may be captured in a CUDA graph.  Calls on
  * one context (forces, prune, adjoint) must not overlap on the GPU: they share
- * the context's layout, accumulators and work-item counter. */
+ * the context's layout, accumulators and work-item counter.  The type-pair
+ * tables live in shared memory; beyond about 40 types they exceed 48 KB and the
+ * kernel runs at lower occupancy. */
 nb_status nb_forces(nb_ctx *ctx, unsigned flags, const float *x_dev, float *f_dev, double *e_dev,
                     double *vir_dev, void *stream);
 
@@ -167,7 +169,9 @@ nb_status nb_forces(nb_ctx *ctx, unsigned flags, const float *x_dev, float *f_de
  * recomputes every pair of the inner list at x_dev and writes gx_dev [N*3],
  * gq_dev [N] (FP32, overwritten) and gc6_dev / gc12_dev [T*T] (FP64,
  * overwritten).  A type pair a != b puts half of its parameter gradient in
- * [a][b] and half in [b][a].  Asynchronous; never allocates. */
+ * [a][b] and half in [b][a].  Supports up to 16 atom types (the parameter
+ * gradients are accumulated in shared memory); more types return
+ * NB_ERR_INVALID_ARG.  Asynchronous; never allocates. */
 nb_status nb_forces_vjp(nb_ctx *ctx, const float *x_dev, const float *gF_dev, double gE,
                         float *gx_dev, float *gq_dev, double *gc6_dev, double *gc12_dev,
                         void *stream);
