@@ -151,9 +151,10 @@ __global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__res
 template <int COUL, bool EN, bool VIR>
 void launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
     const size_t smem = (sizeof(float2) + (EN ? sizeof(float4) : 0)) * v.T * v.T;
-    // the type-pair tables of many types exceed the default 48 KB of dynamic shared
-    // memory (64 types: 96 KB); opt in to the larger carve-out, at lower occupancy
-    if (smem > 48 * 1024)
+    // the type-pair tables of many types, with the 17 KB of static staging arrays,
+    // exceed the default 48 KB of shared memory (64 types: 96 KB of tables); opt in
+    // to the larger carve-out, at lower occupancy
+    if (smem > 16 * 1024)
         cudaFuncSetAttribute(k_forces<COUL, EN, VIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_forces<COUL, EN, VIR>, kFW * 32, smem) != cudaSuccess ||

@@ -11,10 +11,15 @@
 // with phi = -(1/r) dV/dr, phi_C = qi qj psi_C, V_C = qi qj v_C.  The loop
 // structure is the force kernel's: one warp per work item, lanes (ti, tj)
 // over the 8x8 cluster pair, i-gradients in registers, j-gradients reduced
-// over the ti lanes per j-entry.  Parameter gradients are accumulated per warp
-// in shared memory (FP32, one item), then added to an FP64 table; the table is
-// symmetrised at the end so that a type pair a != b puts half of its gradient
-// in [a][b] and half in [b][a] (the pair parameter is (C[a][b] + C[b][a]) / 2).
+// over the ti lanes per j-entry.  Parameter gradients are accumulated in shared
+// memory (FP32, one item), then added to an FP64 table; the table is symmetrised
+// at the end so that a type pair a != b puts half of its gradient in [a][b] and
+// half in [b][a] (the pair parameter is (C[a][b] + C[b][a]) / 2).  With up to 8
+// atom types every lane owns a column of the accumulators ([type pair][33],
+// conflict-free) and the warp folds the columns once per item; with more types
+// the lanes add into one table per warp with shared-memory atomics.  (A few type
+// pairs shared by all 32 lanes serialise such atomics: on the 6-type 24k water box
+// they took two thirds of the kernel.)
 #include "nb_pair.cuh"
 
 using namespace nbk;
@@ -22,7 +27,9 @@ using namespace nbk;
 namespace {
 
 constexpr int kVW = 4;
-constexpr int kVjpMaxT = 16;  // shared-memory parameter accumulators (T*T per warp)
+constexpr int kVjpMaxT = 16;     // shared-memory parameter accumulators (T*T per warp)
+constexpr int kVjpPrivMaxT = 8;  // per-lane accumulator columns up to this many types
+constexpr int kColStride = 33;   // column stride of the per-lane accumulators (bank-conflict free)
 
 struct VjpView {
     SysView s;
@@ -34,20 +41,29 @@ struct VjpView {
     float two_beta_sqrtpi;  // 2 beta / sqrt(pi)
 };
 
-template <int COUL>
+template <int COUL, bool PRIV>
 __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v) {
     __shared__ float4 s_xi[kVW][NB_SCA];
     __shared__ float4 s_gi[kVW][NB_SCA];
     __shared__ int s_ti[kVW][NB_SCA];
-    __shared__ float s_g6[kVW][kVjpMaxT * kVjpMaxT], s_g12[kVW][kVjpMaxT * kVjpMaxT];
     __shared__ float4 s_lje[kVjpMaxT * kVjpMaxT];
+    extern __shared__ float s_par[];  // PRIV: [kVW][2][T*T][33]; else [kVW][2][T*T]
     const SysView &sv = v.s;
     const int T = sv.T, TT = T * T;
     for (int t = threadIdx.x; t < TT; t += blockDim.x) s_lje[t] = sv.lje[t];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    for (int t = lane; t < TT; t += 32) {
-        s_g6[wib][t] = 0.f;
-        s_g12[wib][t] = 0.f;
+    float *const p6 = s_par + (size_t)wib * 2 * TT * (PRIV ? kColStride : 1);
+    float *const p12 = p6 + TT * (PRIV ? kColStride : 1);
+    if (PRIV) {
+        for (int t = 0; t < TT; t++) {
+            p6[t * kColStride + lane] = 0.f;
+            p12[t * kColStride + lane] = 0.f;
+        }
+    } else {
+        for (int t = lane; t < TT; t += 32) {
+            p6[t] = 0.f;
+            p12[t] = 0.f;
+        }
     }
     __syncthreads();
     const int w = blockIdx.x * kVW + wib;
@@ -152,9 +168,12 @@ __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v) {
                 ajy[h] -= gyv;
                 ajz[h] -= gzv;
                 ajq[h] += xi.w * gqc;
-                if (in) {
-                    atomicAdd(&s_g6[wib][ta * T + tjt[h]], g6);
-                    atomicAdd(&s_g12[wib][ta * T + tjt[h]], g12);
+                if (PRIV) {  // g6, g12 are zero for pairs outside rc
+                    p6[(ta * T + tjt[h]) * kColStride + lane] += g6;
+                    p12[(ta * T + tjt[h]) * kColStride + lane] += g12;
+                } else if (in) {
+                    atomicAdd(&p6[ta * T + tjt[h]], g6);
+                    atomicAdd(&p12[ta * T + tjt[h]], g12);
                 }
             }
         }
@@ -191,7 +210,16 @@ __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v) {
     }
     __syncwarp();
     for (int t = lane; t < TT; t += 32) {
-        const float a = s_g6[wib][t], b = s_g12[wib][t];
+        float a = 0.f, b = 0.f;
+        if (PRIV) {  // lane t folds row t over the 32 lane columns (banks (t + l) mod 32)
+            for (int l = 0; l < 32; l++) {
+                a += p6[t * kColStride + l];
+                b += p12[t * kColStride + l];
+            }
+        } else {
+            a = p6[t];
+            b = p12[t];
+        }
         if (a != 0.f) atomicAdd(&v.gpar[t], (double)a);
         if (b != 0.f) atomicAdd(&v.gpar[TT + t], (double)b);
     }
@@ -257,6 +285,13 @@ __global__ void k_vjp_finish(int n, const int *__restrict__ inv, const float4 *_
     }
 }
 
+template <int COUL, bool PRIV>
+void launch_vjp(const VjpView &v, int nb, size_t smem, cudaStream_t st) {
+    // the default limit of 48 KB covers static and dynamic shared memory together
+    if (smem > 16 * 1024) cudaFuncSetAttribute(k_vjp<COUL, PRIV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_vjp<COUL, PRIV><<<nb, kVW * 32, smem, st>>>(v);
+}
+
 }  // namespace
 
 nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, float *gx, float *gq, double *gc6,
@@ -281,12 +316,24 @@ nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, f
         NbTraceScope tr(c, NB_TRACE_VJP, st);
         c->n_launches++;
         const int nb = (v.s.n_items + kVW - 1) / kVW;
-        if (c->coulomb == NB_COULOMB_RF)
-            k_vjp<NB_COULOMB_RF><<<nb, kVW * 32, 0, st>>>(v);
-        else if (c->coulomb == NB_COULOMB_EWALD)
-            k_vjp<NB_COULOMB_EWALD><<<nb, kVW * 32, 0, st>>>(v);
-        else
-            k_vjp<NB_COULOMB_NONE><<<nb, kVW * 32, 0, st>>>(v);
+        const int TT = c->T * c->T;
+        if (c->T <= kVjpPrivMaxT) {
+            const size_t smem = sizeof(float) * kVW * 2 * TT * kColStride;
+            if (c->coulomb == NB_COULOMB_RF)
+                launch_vjp<NB_COULOMB_RF, true>(v, nb, smem, st);
+            else if (c->coulomb == NB_COULOMB_EWALD)
+                launch_vjp<NB_COULOMB_EWALD, true>(v, nb, smem, st);
+            else
+                launch_vjp<NB_COULOMB_NONE, true>(v, nb, smem, st);
+        } else {
+            const size_t smem = sizeof(float) * kVW * 2 * TT;
+            if (c->coulomb == NB_COULOMB_RF)
+                launch_vjp<NB_COULOMB_RF, false>(v, nb, smem, st);
+            else if (c->coulomb == NB_COULOMB_EWALD)
+                launch_vjp<NB_COULOMB_EWALD, false>(v, nb, smem, st);
+            else
+                launch_vjp<NB_COULOMB_NONE, false>(v, nb, smem, st);
+        }
     }
     const int nf = c->N > c->T * c->T ? c->N : c->T * c->T;
     k_vjp_finish<<<(nf + 255) / 256, 256, 0, st>>>(c->N, c->inv, c->gxs, c->gqs, gx, gq, c->T, c->gpar, gc6, gc12);

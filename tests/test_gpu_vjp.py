@@ -54,6 +54,18 @@ def test_vjp_small_box(api, coulomb):
     check(g, r)
 
 
+@pytest.mark.parametrize("n_extra", [6, 10])
+def test_vjp_many_types(api, n_extra):
+    """8 types (per-lane parameter accumulators, the largest such case) and 12 types
+    (shared-memory atomics)."""
+    rng = np.random.default_rng(3 + n_extra)
+    extra = [(0.3166 * rng.uniform(0.9, 1.1), 0.65 * rng.uniform(0.7, 1.3)) for _ in range(n_extra)]
+    s = synth.water_box(1000, 3.1, seed=53, coulomb=synth.COULOMB_EWALD, rc=1.0, rlist=1.1, extra_o_types=extra)
+    assert s.n_types == 2 + n_extra
+    gF = rng.normal(size=(s.n, 3))
+    check(gpu_vjp(api, s, gF, 0.4), oracle.vjp(s, gF, 0.4))
+
+
 def test_vjp_24k_six_types(api):
     s = synth.water_24k_types()
     rng = np.random.default_rng(2)
