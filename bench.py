@@ -402,7 +402,34 @@ def extra_workloads(args):
         "kernels_per_step": "gather, k_forces, unsort | memset, spread, FFT R2C (cuFFT), solve, FFT C2R (cuFFT), "
                             "gather | corrections",
     }
-    del gfull, pme, c2
+    del gfull, pme
+    # first use of a new list: separate full prune + force call on the inner list, against
+    # the force call that evaluates the outer list and prunes on the way (nb_set_fused_prune)
+    def ev_time(fn):
+        a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush()
+        a.record()
+        fn()
+        bb.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(bb)
+
+    sep_ms, fus_ms, plain_ms = [], [], []
+    cf = api.NbContext.from_system(s2)
+    cf.nb_set_fused_prune(True)
+    for rep in range(8):
+        c2.nb_set_fused_prune(False)
+        c2.build(x2, s2.box)
+        sep_ms.append(ev_time(lambda: c2.nb_prune_rolling(0, 1)) + ev_time(sr))
+        plain_ms.append(ev_time(sr))
+        cf.build(x2, s2.box)
+        fus_ms.append(ev_time(lambda: cf.nb_forces(fl, x2, f2, e_sr, w_sr)))
+    out["first_use_prune_96k"] = {
+        "separate_prune_plus_forces_ms": float(np.median(sep_ms[2:])),
+        "fused_forces_on_outer_list_ms": float(np.median(fus_ms[2:])),
+        "forces_on_inner_list_ms": float(np.median(plain_ms[2:])),
+    }
+    del c2, cf
     # LJ argon throughput against the number of pairs per particle (the paper's Fig. 6
     # system: 157k atoms, rho 26 nm^-3, sigma 0.3345 nm; force-only, LJ-only kernel)
     sweep = []

@@ -180,6 +180,7 @@ nb_status nb_forces_vjp(nb_ctx *ctx, const float *x_dev, const float *gF_dev, do
  * (Sec. VI ensembles sharing a GPU; tail balancing of Sec. V.F).  The batch
  * refers to (does not own) `n` contexts that already have pair lists and the
  * same Coulomb type; it must be re-created after any of them is re-built.
+ * A pending fused first-use prune (nb_set_fused_prune) is completed here.
  * Allocates in nb_batch_create only. */
 nb_status nb_batch_create(nb_ctx *const *ctxs, int n, nb_batch **out);
 void nb_batch_destroy(nb_batch *batch);
@@ -213,6 +214,16 @@ nb_status nb_debug_layout(nb_ctx *ctx, int32_t *perm_host, float *xq_host, float
                           void *stream);
 
 nb_status nb_get_stats(nb_ctx *ctx, nb_stats *out);
+
+/* First-use prune fused into the force kernel (Sec. V.D), off by default.  When
+ * on, nb_pairlist_build does not prune; the next nb_forces evaluates the outer
+ * list, records on the way which (i-cluster, j-half) blocks have an atom pair
+ * closer than r_in at that call's positions, and compacts them into the inner
+ * list (the same list the separate prune gives at those positions).  Calls that
+ * need the inner list before that force call (nb_prune_rolling, nb_forces_vjp,
+ * nb_forces_batched, inner-list counts and exports) prune it first.  Takes effect
+ * at the next nb_pairlist_build.  on: 0 or 1. */
+nb_status nb_set_fused_prune(nb_ctx *ctx, int on);
 
 /* Tuning (Sec. V.F: lists are split when there are too few of them for the GPU):
  * the largest number of outer j-cluster entries per work item (4..128, default

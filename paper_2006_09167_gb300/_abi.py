@@ -36,7 +36,7 @@ EXPORTED = [
     "nb_forces_batched", "nb_count_pairs", "nb_debug_export_pairs", "nb_debug_layout",
     "nb_get_stats", "nb_get_error", "nb_status_str", "nb_trace_enable", "nb_trace_read",
     "nb_forces_small_noalloc", "nb_set_split", "nb_pme_create", "nb_pme_destroy", "nb_pme_forces",
-    "nb_ewald_corrections",
+    "nb_ewald_corrections", "nb_set_fused_prune",
 ]
 NB_NOALLOC_MAX_ATOMS = 16384
 NB_NOALLOC_MAX_TYPES = 8
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
     lib.nb_get_stats.argtypes = [vp, ctypes.POINTER(NbStats)]
     lib.nb_get_error.argtypes = [vp, vp]
     lib.nb_set_split.argtypes = [vp, ctypes.c_int]
+    lib.nb_set_fused_prune.argtypes = [vp, ctypes.c_int]
     lib.nb_trace_enable.argtypes = [vp, ctypes.c_int]
     lib.nb_trace_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p]
     lib.nb_forces_small_noalloc.argtypes = [ctypes.POINTER(NbParams), vp, vp, vp, vp, vp,

@@ -170,6 +170,10 @@ class NbContext:
         check(self._lib.nb_get_stats(self.handle, ctypes.byref(s)), "nb_get_stats")
         return {k: int(getattr(s, k)) for k, _ in _abi.NbStats._fields_}
 
+    def nb_set_fused_prune(self, on: bool = True):
+        """First prune after each list build inside the next force call (nb_set_fused_prune)."""
+        check(self._lib.nb_set_fused_prune(self.handle, int(bool(on))), "nb_set_fused_prune")
+
     def nb_set_split(self, split: int):
         check(self._lib.nb_set_split(self.handle, int(split)), "nb_set_split")
 

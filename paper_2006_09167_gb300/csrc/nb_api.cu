@@ -116,6 +116,8 @@ nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     v.rc6inv = (float)rc6;
     v.rc12inv = (float)(rc6 * rc6);
     v.queue = c->queue;
+    v.kept = nullptr;
+    v.rin2 = 0.f;
     v.ew_beta2 = (float)(c->beta * c->beta);
     v.ew_2bsp = (float)(2.0 * c->beta / sqrt(M_PI));
     return v;
@@ -446,7 +448,12 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
     if ((s = nb_launch_search_write(c, rlist, st)) != NB_OK) return s;
     c->split_built = c->split;
     c->rlist_built = rlist;
-    if ((s = nb_launch_prune(c, (float)c->r_in, 0, 1, st)) != NB_OK) return s;
+    c->inner_pending = false;
+    if (c->fused_prune) {
+        c->inner_pending = true;  // pruned by the next force call
+    } else if ((s = nb_launch_prune(c, (float)c->r_in, 0, 1, st)) != NB_OK) {
+        return s;
+    }
     NB_CUDA_TRY(cudaStreamSynchronize(st));
     c->have_list = true;
     return NB_OK;
@@ -457,6 +464,8 @@ nb_status nb_prune_rolling(nb_ctx *c, float r_in, int part, int n_parts, void *s
     if (!c->have_list) return NB_ERR_NOT_READY;
     if (n_parts < 1 || part < 0 || part >= n_parts) return NB_ERR_INVALID_ARG;
     if (!(r_in >= (float)c->rc) || !(r_in <= c->rlist_built)) return NB_ERR_INVALID_ARG;
+    nb_status s = nb_ensure_inner(c, (cudaStream_t)stream);
+    if (s != NB_OK) return s;
     return nb_launch_prune(c, r_in, part, n_parts, (cudaStream_t)stream);
 }
 
@@ -471,6 +480,12 @@ nb_status nb_forces(nb_ctx *c, unsigned flags, const float *x_dev, float *f_dev,
     nb_status s = nb_launch_gather(c, x_dev, (flags & NB_ENERGY) ? e_dev : nullptr,
                                    (flags & NB_VIRIAL) ? vir_dev : nullptr, st);
     if (s != NB_OK) return s;
+    if (c->inner_pending) {  // first use of a new list: forces from the outer list, pruned on the way
+        if ((s = nb_launch_forces(c, flags, f_dev, e_dev, vir_dev, st, true)) != NB_OK) return s;
+        if ((s = nb_launch_prune_compact_all(c, st)) != NB_OK) return s;
+        c->inner_pending = false;
+        return NB_OK;
+    }
     return nb_launch_forces(c, flags, f_dev, e_dev, vir_dev, st);
 }
 
@@ -479,6 +494,7 @@ nb_status nb_forces_vjp(nb_ctx *c, const float *x_dev, const float *gF_dev, doub
     if (!c || !x_dev || !gF_dev || !gx_dev || !gq_dev || !gc6_dev || !gc12_dev) return NB_ERR_INVALID_ARG;
     if (!isfinite(gE)) return NB_ERR_INVALID_ARG;
     if (!c->have_list) return NB_ERR_NOT_READY;
+    if (nb_status s = nb_ensure_inner(c, (cudaStream_t)stream); s != NB_OK) return s;
     return nb_launch_vjp(c, x_dev, gF_dev, gE, gx_dev, gq_dev, gc6_dev, gc12_dev, (cudaStream_t)stream);
 }
 
@@ -487,7 +503,9 @@ nb_status nb_count_pairs(nb_ctx *c, int which, int64_t *n_within, int64_t *n_eva
     if (which != NB_LIST_OUTER && which != NB_LIST_INNER) return NB_ERR_INVALID_ARG;
     if (!c->have_list) return NB_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;
-    nb_status s = nb_launch_count(c, which, st);
+    nb_status s = which == NB_LIST_INNER ? nb_ensure_inner(c, st) : NB_OK;
+    if (s != NB_OK) return s;
+    s = nb_launch_count(c, which, st);
     if (s != NB_OK) return s;
     long long h[2];
     NB_CUDA_TRY(cudaMemcpyAsync(h, c->diag, 2 * sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -502,6 +520,10 @@ nb_status nb_debug_export_pairs(nb_ctx *c, int which, int64_t *buf_host, size_t 
     if (which != NB_LIST_OUTER && which != NB_LIST_INNER) return NB_ERR_INVALID_ARG;
     if (!c->have_list) return NB_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;
+    if (which == NB_LIST_INNER) {
+        const nb_status s0 = nb_ensure_inner(c, st);
+        if (s0 != NB_OK) return s0;
+    }
     long long *d = nullptr;
     NB_CUDA_TRY(cudaMalloc(&d, sizeof(long long) * (1 + 5 * (size_t)cap)));
     nb_status s = nb_launch_export(c, which, d + 1, (long long)cap, d, st);
@@ -531,6 +553,12 @@ nb_status nb_debug_layout(nb_ctx *c, int32_t *perm_host, float *xq_host, float *
         NB_CUDA_TRY(cudaMemcpyAsync(bbox_host, c->bb, sizeof(float4) * 2 * (size_t)c->S_host * NB_SCL,
                                     cudaMemcpyDeviceToHost, st));
     NB_CUDA_TRY(cudaStreamSynchronize(st));
+    return NB_OK;
+}
+
+nb_status nb_set_fused_prune(nb_ctx *c, int on) {
+    if (!c || (on != 0 && on != 1)) return NB_ERR_INVALID_ARG;
+    c->fused_prune = on != 0;
     return NB_OK;
 }
 

@@ -162,6 +162,13 @@ nb_status nb_batch_create(nb_ctx *const *ctxs, int n, nb_batch **out) {
         if (!ctxs[r]->have_list) return NB_ERR_NOT_READY;
         if (ctxs[r]->coulomb != ctxs[0]->coulomb) return NB_ERR_INVALID_ARG;
     }
+    // the batched kernel reads the inner lists: finish any pending first-use prune
+    for (int r = 0; r < n; r++) {
+        if (!ctxs[r]->inner_pending) continue;
+        const nb_status s = nb_ensure_inner(ctxs[r], 0);
+        if (s != NB_OK) return s;
+        if (cudaStreamSynchronize(0) != cudaSuccess) return nb_cuda_status(cudaGetLastError());
+    }
     nb_batch *b = new (std::nothrow) nb_batch();
     if (!b) return NB_ERR_INVALID_ARG;
     b->R = n;

@@ -33,7 +33,7 @@ constexpr int kFW = 4;  // warps (work items) per block
 // Persistent: a grid sized to the resident capacity of the GPU, each warp taking
 // the next work item (ordered longest first) from a device counter, so the
 // kernel tail is at most one item long (paper Sec. V.F: tails from uneven work).
-template <int COUL, bool EN, bool VIR>
+template <int COUL, bool EN, bool VIR, bool PRUNE = false>
 __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
     extern __shared__ float4 s_dyn[];
     float4 *s_lje = s_dyn;                                                  // EN only: [T*T]
@@ -53,12 +53,13 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
     const int n_warps = gridDim.x * kFW;
     int w = blockIdx.x * kFW + wib;
     while (w < v.n_items) {
-        const int nj = v.inner_len[w];
+        const int nj = PRUNE ? v.items[w].w : v.inner_len[w];
         KSum elj, ec;
         float vr[9];
 #pragma unroll
         for (int k = 0; k < 9; k++) vr[k] = 0.f;
-        if (nj > 0) process_item<COUL, EN, VIR>(v, w, nj, s_lj, s_lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
+        if (nj > 0)
+            process_item<COUL, EN, VIR, PRUNE>(v, w, nj, s_lj, s_lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
         if (EN || VIR) {
             // FP32 warp reduction; one row of 11 partial sums per work item, reduced in
             // FP64 by the unsort kernel (no block barrier, no same-address atomics)
@@ -148,20 +149,20 @@ __global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__res
     }
 }
 
-template <int COUL, bool EN, bool VIR>
+template <int COUL, bool EN, bool VIR, bool PRUNE = false>
 void launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
     const size_t smem = (sizeof(float2) + (EN ? sizeof(float4) : 0)) * v.T * v.T;
     // the type-pair tables of many types, with the 17 KB of static staging arrays,
     // exceed the default 48 KB of shared memory (64 types: 96 KB of tables); opt in
     // to the larger carve-out, at lower occupancy
     if (smem > 16 * 1024)
-        cudaFuncSetAttribute(k_forces<COUL, EN, VIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_forces<COUL, EN, VIR, PRUNE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_forces<COUL, EN, VIR>, kFW * 32, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_forces<COUL, EN, VIR, PRUNE>, kFW * 32, smem) != cudaSuccess ||
         occ < 1)
         occ = 1;
     const int blocks = std::min((v.n_items + kFW - 1) / kFW, std::max(n_sm, 1) * occ);
-    k_forces<COUL, EN, VIR><<<blocks, kFW * 32, smem, st>>>(v);
+    k_forces<COUL, EN, VIR, PRUNE><<<blocks, kFW * 32, smem, st>>>(v);
 }
 
 }  // namespace
@@ -198,12 +199,25 @@ void nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, int n_sm,
 
 int nb_force_blocks(int n_items) { return n_items; }  // rows of per-item partial sums
 
-nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, double *vir, cudaStream_t st) {
+nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, double *vir, cudaStream_t st,
+                           bool fused_prune) {
     const bool red = flags & (NB_ENERGY | NB_VIRIAL);
     SysView v = nb_make_view(c, c->fs, (flags & NB_ENERGY) ? e : nullptr, (flags & NB_VIRIAL) ? vir : nullptr);
     if (v.n_items > 0) {
         NbTraceScope tr(c, NB_TRACE_FORCES, st);
-        nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
+        if (fused_prune) {
+            // first use of a new list: the outer list, pruned on the way (energy and
+            // virial rows are always formed; they are folded only if requested)
+            v.cj = c->cj_outer;
+            v.kept = c->kept;
+            const float re = (float)c->r_in * (1.0f + 2e-6f);  // as the separate prune pass
+            v.rin2 = re * re;
+            if (c->coulomb == NB_COULOMB_RF) launch_forces_t<NB_COULOMB_RF, true, true, true>(v, c->n_sm, st);
+            else if (c->coulomb == NB_COULOMB_EWALD) launch_forces_t<NB_COULOMB_EWALD, true, true, true>(v, c->n_sm, st);
+            else launch_forces_t<NB_COULOMB_NONE, true, true, true>(v, c->n_sm, st);
+        } else {
+            nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
+        }
         c->n_launches++;
     }
     const int nb = (c->N + 255) / 256;

@@ -66,6 +66,8 @@ struct SysView {
     float ew_2bsp;   // 2 beta / sqrt(pi)
     float rc6inv, rc12inv;
     int *queue;  // work-item counter of the persistent force kernel (zeroed by the gather)
+    unsigned short *kept;  // first-use prune fused into the force kernel: half masks per outer entry
+    float rin2;            // and its squared inner radius
 };
 
 // inner-entry decoding
@@ -154,6 +156,8 @@ struct nb_ctx {
     // lists
     bool have_list = false;
     float rlist_built = 0.f;
+    bool fused_prune = false;    // first prune after a build inside the first force call
+    bool inner_pending = false;  // the inner list awaits that first prune
     int split = 16;          // max outer j-entries per work item (next build)
     int split_built = 16;    // max outer j-entries per work item of the current lists
     int n_items = 0, n_j = 0, n_masks = 0;
@@ -216,8 +220,10 @@ nb_status nb_launch_grid_sort(nb_ctx *c, const float *x, cudaStream_t st);
 nb_status nb_launch_search(nb_ctx *c, float rlist, cudaStream_t st);
 nb_status nb_launch_prune(nb_ctx *c, float r_in, int part, int n_parts, cudaStream_t st);
 nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cudaStream_t st);
+nb_status nb_launch_prune_compact_all(nb_ctx *c, cudaStream_t st);
+nb_status nb_ensure_inner(nb_ctx *c, cudaStream_t st);
 nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, double *vir,
-                           cudaStream_t st);
+                           cudaStream_t st, bool fused_prune = false);
 nb_status nb_launch_count(nb_ctx *c, int which, cudaStream_t st);
 nb_status nb_launch_export(nb_ctx *c, int which, long long *buf, long long cap, long long *count,
                            cudaStream_t st);

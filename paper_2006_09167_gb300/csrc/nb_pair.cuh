@@ -300,7 +300,12 @@ __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__re
 // walks the set bits of the interaction mask (a warp-uniform loop) and is not
 // unrolled, so the kernel stays small enough for the instruction cache and the
 // i-forces of the 8 clusters live in shared memory rather than in registers.
-template <int COUL, bool EN, bool VIR>
+//
+// PRUNE (first use of a new list, Sec. V.D): the entries are the outer list's
+// (one 8-bit mask for both j-halves); while computing the forces the warp also
+// records, per i-cluster and j-half, whether any atom pair is closer than r_in,
+// and writes those half masks to v.kept for the compaction into the inner list.
+template <int COUL, bool EN, bool VIR, bool PRUNE = false>
 __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, const float2 *ljt, const float4 *lje,
                                              float4 *s_xi, int *s_ti, float *s_fi, KSum &elj, KSum &ec,
                                              float (&vr)[9]) {
@@ -325,8 +330,9 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
 
     for (int e = 0; e < nj; e++) {
         const int2 ent = v.cj[j0 + e];
-        const int cj = inner_cj(ent), mg = entry_group(ent);
-        const int lo = inner_lo(ent), hi = inner_hi(ent);
+        const int cj = PRUNE ? ent.x : inner_cj(ent), mg = entry_group(ent);
+        const int lo = PRUNE ? (ent.y & 0xff) : inner_lo(ent), hi = PRUNE ? lo : inner_hi(ent);
+        int keep_lo = 0, keep_hi = 0;  // PRUNE: half masks that survive r_in
         float4 xj0 = v.xq[cj * NB_CL + tj], xj1 = v.xq[cj * NB_CL + tj + 4];
         if (sh.jshift) {
             xj0 = shift_j(xj0, sh);
@@ -354,6 +360,11 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             const float4 xi = s_xi[k * NB_CL + ti];
             const int tio = s_ti[k * NB_CL + ti];
             const float2 dx = psub(p2(xi.x), jx), dy = psub(p2(xi.y), jy), dz = psub(p2(xi.z), jz);
+            if (PRUNE) {  // same distances, same rounding as the separate prune pass
+                const float2 r2 = pfma(dz, dz, pfma(dy, dy, pmul(dx, dx)));
+                keep_lo |= (int)__any_sync(full, r2.x < v.rin2) << k;
+                keep_hi |= (int)__any_sync(full, r2.y < v.rin2) << k;
+            }
             const float2 p = pair_phi2<COUL, EN>(v, ljt, lje, dx, dy, dz, xi.w, jq, tio + tj0, tio + tj1, b0, b1,
                                                  elj2, ec2);
             const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
@@ -401,6 +412,7 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             elj_e += elj2.x + elj2.y;
             ec_e += ec2.x + ec2.y;
         }
+        if (PRUNE && lane == 0) v.kept[j0 + e] = (unsigned short)(keep_lo | (keep_hi << 8));
         const float f0x = fjx.x, f0y = fjy.x, f0z = fjz.x, f1x = fjx.y, f1y = fjy.y, f1z = fjz.y;
         if (EN) {
             elj.add(elj_e);

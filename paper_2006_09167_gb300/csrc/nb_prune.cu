@@ -249,6 +249,38 @@ nb_status nb_launch_prune(nb_ctx *c, float r_in, int part, int n_parts, cudaStre
     return NB_OK;
 }
 
+// Compaction of every item's outer entries by the masks in c->kept (after the
+// fused first-use prune of the force kernel).
+nb_status nb_launch_prune_compact_all(nb_ctx *c, cudaStream_t st) {
+    if (c->n_items == 0) return NB_OK;
+    PruneArgs a;
+    a.n_items = c->n_items;
+    a.part = 0;
+    a.n_parts = 1;
+    a.items = c->items;
+    a.cj_outer = c->cj_outer;
+    a.xq = c->xq;
+    box_split(c, a.Lhi, a.Llo);
+    a.rin2 = 0.f;
+    a.cj_inner = c->cj_inner;
+    a.inner_len = c->inner_len;
+    a.kept = c->kept;
+    c->n_launches++;
+    k_prune_compact<<<(unsigned)((c->n_items + kPW - 1) / kPW), kPW * 32, 0, st>>>(a);
+    NB_CUDA_TRY(cudaGetLastError());
+    return NB_OK;
+}
+
+// Calls that need the inner list while its fused first-use prune is still
+// pending prune the whole outer list first, at the positions of the last sort
+// or force call.
+nb_status nb_ensure_inner(nb_ctx *c, cudaStream_t st) {
+    if (!c->inner_pending) return NB_OK;
+    const nb_status s = nb_launch_prune(c, (float)c->r_in, 0, 1, st);
+    if (s == NB_OK) c->inner_pending = false;
+    return s;
+}
+
 nb_status nb_launch_count(nb_ctx *c, int which, cudaStream_t st) {
     NB_CUDA_TRY(cudaMemsetAsync(c->diag, 0, 2 * sizeof(long long), st));
     if (c->n_items == 0) return NB_OK;
