@@ -79,13 +79,26 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
     }
 }
 
+// Lines the force kernel will read from memory the gather does not write (inner
+// list, item table, sorted types, exclusion masks): prefetched into L2 by the
+// gather, so the force kernel's per-entry loads do not each wait for DRAM when
+// the cache is cold.
+struct L2Prefetch {
+    const char *p[5];
+    long long lines[5];  // 128-byte lines per region
+};
+
 // Positions of the step into the cluster layout (image offsets of the last sort),
-// zeroing of the force accumulators and of the energy / virial outputs.
+// zeroing of the force accumulators and of the energy / virial outputs, and L2
+// prefetch of the lists.
 __global__ void k_gather(int nslots, const int *__restrict__ perm, const float *__restrict__ x,
                          const int *__restrict__ img, const float *__restrict__ q_s, double Lx, double Ly,
                          double Lz, float4 *__restrict__ xq, float4 *__restrict__ fs, double *e, double *vir,
-                         int *err, int *queue) {
+                         int *err, int *queue, L2Prefetch pf) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < 5; r++)
+        if (s < pf.lines[r]) asm volatile("prefetch.global.L2 [%0];" ::"l"(pf.p[r] + (size_t)s * 128));
     if (s == 0) {
         *queue = 0;
         if (e) e[0] = e[1] = 0.0;
@@ -171,8 +184,22 @@ nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cu
     const int ns = c->S_host * NB_SCA;
     NbTraceScope tr(c, NB_TRACE_GATHER, st);
     c->n_launches++;
-    k_gather<<<(ns + 255) / 256, 256, 0, st>>>(ns, c->perm, x, c->img, c->q_s, c->box[0], c->box[1],
-                                                c->box[2], c->xq, c->fs, e, vir, c->err, c->queue);
+    L2Prefetch pf;
+    const bool lists = c->have_list;
+    const void *base[5] = {c->cj_inner, c->items, c->inner_len, c->type_s, c->masks};
+    const long long bytes[5] = {lists ? (long long)c->n_j * 8 : 0, lists ? (long long)c->n_items * 16 : 0,
+                                lists ? (long long)c->n_items * 4 : 0, (long long)ns * 4,
+                                lists ? (long long)c->n_masks * 64 : 0};
+    long long most = 0;
+    for (int r = 0; r < 5; r++) {
+        pf.p[r] = (const char *)base[r];
+        pf.lines[r] = base[r] ? (bytes[r] + 127) / 128 : 0;
+        most = std::max(most, pf.lines[r]);
+    }
+    const long long threads = std::max<long long>(ns, most);
+    k_gather<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ns, c->perm, x, c->img, c->q_s, c->box[0], c->box[1],
+                                                                c->box[2], c->xq, c->fs, e, vir, c->err, c->queue,
+                                                                pf);
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
 }

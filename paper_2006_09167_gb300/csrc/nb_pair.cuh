@@ -230,12 +230,12 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
     return phi;
 }
 
-// Two pairs (i, j0) and (i, j1) at once: pair_phi's operations, in the same
-// order, on float2 values (component 0: j0, component 1: j1).  Energies are added
-// per component to elj / ec.
+// Two pairs at once: pair_phi's operations, in the same order, on float2 values
+// (component 0: the first pair, component 1: the second; i-charges qi and
+// j-charges qj per component).  Energies are added per component to elj / ec.
 template <int COUL, bool EN>
 __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__restrict__ ljt,
-                                            const float4 *__restrict__ lje, float2 dx, float2 dy, float2 dz, float qi,
+                                            const float4 *__restrict__ lje, float2 dx, float2 dy, float2 dz, float2 qi,
                                             float2 qj, int tp0, int tp1, bool b0, bool b1, float2 &elj, float2 &ec) {
     float2 r2 = pfma(dz, dz, pfma(dy, dy, pmul(dx, dx)));
     const bool in0 = b0 && (r2.x < v.rc2), in1 = b1 && (r2.y < v.rc2);
@@ -250,7 +250,7 @@ __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__re
     const float2 rinv6 = pmul(pmul(rinv2, rinv2), rinv2);
     const float2 la = ljt[tp0], lb = ljt[tp1];  // (6 C6, 12 C12)
     const float2 flj = pmul(rinv6, pfma(make_float2(la.y, lb.y), rinv6, make_float2(-la.x, -lb.x)));
-    const float2 qq = pmul(p2(qi), qj);
+    const float2 qq = pmul(qi, qj);
     float2 fc = p2(0.f), erfcz = p2(0.f);
     if (COUL == NB_COULOMB_RF) {
         fc = pmul(qq, pfma(rinv, rinv2, p2(-2.0f * v.k_rf)));
@@ -365,8 +365,8 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
                 keep_lo |= (int)__any_sync(full, r2.x < v.rin2) << k;
                 keep_hi |= (int)__any_sync(full, r2.y < v.rin2) << k;
             }
-            const float2 p = pair_phi2<COUL, EN>(v, ljt, lje, dx, dy, dz, xi.w, jq, tio + tj0, tio + tj1, b0, b1,
-                                                 elj2, ec2);
+            const float2 p = pair_phi2<COUL, EN>(v, ljt, lje, dx, dy, dz, p2(xi.w), jq, tio + tj0, tio + tj1, b0,
+                                                 b1, elj2, ec2);
             const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
             float *fk = s_fi + k * 96 + lane;
             fk[0] += ax.x + ax.y;
@@ -376,12 +376,60 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             fjy = psub(fjy, ay);
             fjz = psub(fjz, az);
         }
-        // i-clusters that the prune kept for one j-half only: one pair per lane
+        // i-clusters that the prune kept for one j-half only: two such i-clusters share a
+        // packed iteration (each component its own i-atom, j-atom and mask bit)
         int one = lo ^ hi;
 #pragma unroll 1
-        while (one) {
-            const int k = __ffs(one) - 1;
+        while (__popc(one) >= 2) {
+            const int ka = __ffs(one) - 1;
             one &= one - 1;
+            const int kb = __ffs(one) - 1;
+            one &= one - 1;
+            const bool ua = (hi >> ka) & 1, ub = (hi >> kb) & 1;  // warp-uniform
+            bool ba = true, bb = true;
+            if (mg) {
+                const unsigned long long* mm = v.masks + (size_t)(mg - 1) * 8;
+                ba = (mm[ka] >> (ti * 8 + tj + (ua ? 4 : 0))) & 1ull;
+                bb = (mm[kb] >> (ti * 8 + tj + (ub ? 4 : 0))) & 1ull;
+            }
+            const float4 xia = s_xi[ka * NB_CL + ti], xib = s_xi[kb * NB_CL + ti];
+            const float4 xja = ua ? xj1 : xj0, xjb = ub ? xj1 : xj0;
+            const float2 dx = psub(make_float2(xia.x, xib.x), make_float2(xja.x, xjb.x));
+            const float2 dy = psub(make_float2(xia.y, xib.y), make_float2(xja.y, xjb.y));
+            const float2 dz = psub(make_float2(xia.z, xib.z), make_float2(xja.z, xjb.z));
+            const float2 p = pair_phi2<COUL, EN>(v, ljt, lje, dx, dy, dz, make_float2(xia.w, xib.w),
+                                                 make_float2(xja.w, xjb.w), s_ti[ka * NB_CL + ti] + (ua ? tj1 : tj0),
+                                                 s_ti[kb * NB_CL + ti] + (ub ? tj1 : tj0), ba, bb, elj2, ec2);
+            const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
+            float *fa = s_fi + ka * 96 + lane;
+            float *fb = s_fi + kb * 96 + lane;
+            fa[0] += ax.x;
+            fa[32] += ay.x;
+            fa[64] += az.x;
+            fb[0] += ax.y;
+            fb[32] += ay.y;
+            fb[64] += az.y;
+            if (ua) {
+                fjx.y -= ax.x;
+                fjy.y -= ay.x;
+                fjz.y -= az.x;
+            } else {
+                fjx.x -= ax.x;
+                fjy.x -= ay.x;
+                fjz.x -= az.x;
+            }
+            if (ub) {
+                fjx.y -= ax.y;
+                fjy.y -= ay.y;
+                fjz.y -= az.y;
+            } else {
+                fjx.x -= ax.y;
+                fjy.x -= ay.y;
+                fjz.x -= az.y;
+            }
+        }
+        if (one) {  // the last single-half i-cluster: one pair per lane
+            const int k = __ffs(one) - 1;
             const bool upper = (hi >> k) & 1;  // warp-uniform
             bool b = true;
             if (mg) {
