@@ -68,7 +68,7 @@ def save_cache(path: Optional[str], cache: dict) -> None:
 
 
 def tune(system, x, velocities=None, *, splits: Sequence[int] = SPLITS, parts: Sequence[int] = PARTS,
-         nstlist: int = 100, dt: float = 0.002, reps: int = 10, cache_path: Optional[str] = None,
+         nstlist: int = 100, dt: float = 0.002, reps: int = 15, cache_path: Optional[str] = None,
          flags: Optional[int] = None, flush: Optional[Callable[[], None]] = None) -> dict:
     """Tune split and n_parts for `system` at positions x (CUDA float32 [N,3]).
 
@@ -88,27 +88,37 @@ def tune(system, x, velocities=None, *, splits: Sequence[int] = SPLITS, parts: S
         return cache[key]
     if flags is None:
         flags = api.NB_ENERGY | api.NB_VIRIAL
-    ctx = api.NbContext.from_system(system)
     f = torch.empty_like(x)
     e = torch.empty(2, dtype=torch.float64, device=x.device)
     w = torch.empty(9, dtype=torch.float64, device=x.device)
-    ctx.nb_trace_enable(True)
-    split_ms = {}
+    # one context per candidate, timed in interleaved rounds (slow drifts of clock or
+    # temperature hit every candidate alike); the median launch time decides
+    ctxs = {}
     for sp in splits:
-        ctx.nb_set_split(sp)
-        ctx.build(x, system.box)
+        c = api.NbContext.from_system(system)
+        c.nb_set_split(sp)
+        c.build(x, system.box)
+        c.nb_trace_enable(True)
         for _ in range(3):
-            ctx.nb_forces(flags, x, f, e, w)
-        torch.cuda.synchronize()
-        ctx.nb_trace_read(api.NB_TRACE_FORCES)
-        for _ in range(reps):
+            c.nb_forces(flags, x, f, e, w)
+        ctxs[sp] = c
+    torch.cuda.synchronize()
+    for c in ctxs.values():
+        c.nb_trace_read(api.NB_TRACE_FORCES)
+    samples = {sp: [] for sp in splits}
+    for _ in range(reps):
+        for sp, c in ctxs.items():
             if flush is not None:
                 flush()
-            ctx.nb_forces(flags, x, f, e, w)
-        ms, n = ctx.nb_trace_read(api.NB_TRACE_FORCES)
-        split_ms[sp] = ms / max(n, 1)
+            c.nb_forces(flags, x, f, e, w)
+            ms, n = c.nb_trace_read(api.NB_TRACE_FORCES)
+            samples[sp].append(ms / max(n, 1))
+    split_ms = {sp: float(sorted(v)[len(v) // 2]) for sp, v in samples.items()}
+    del ctxs
     best_split = choose_split(split_ms)
+    ctx = api.NbContext.from_system(system)
     ctx.nb_set_split(best_split)
+    ctx.nb_trace_enable(True)
     result = {"split": best_split, "split_ms": split_ms, "n_parts": 2, "missed": {}, "step_ms": {}}
     if velocities is not None:
         for npart in parts:
