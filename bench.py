@@ -474,9 +474,23 @@ def cpu_oracle_sample(seconds=12.0):
         oracle.celllist(s)
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same on one host core (a shorter sample: one or two evaluations)
+    oracle.set_num_threads(1)
+    try:
+        n1 = 0
+        t1 = time.perf_counter()
+        while time.perf_counter() - t1 < seconds / 3 or n1 == 0:
+            oracle.celllist(s)
+            n1 += 1
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} full FP64 cell-list evaluations (forces, energies, virial) of the 96,000-atom box "
-                      f"in {dt:.1f} s"}
+                      f"in {dt:.1f} s",
+            "single_core_value": n1 / dt1,
+            "single_core_sample": f"{n1} evaluations on 1 core in {dt1:.1f} s"}
 
 
 def main_ours(args):
