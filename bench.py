@@ -269,7 +269,7 @@ def extra_workloads(args):
     from paper_2006_09167_gb300 import autotune
     flush = l2_flusher(dev)
     xs_tune = [torch.tensor(sysr.x, device=dev) for sysr in reps]
-    tuned_b = autotune.tune_batched(reps, xs_tune, splits=(8, 12, 16, 24, 32, 48, 64), reps=5, flush=flush)
+    tuned_b = autotune.tune_batched(reps, xs_tune, splits=(16, 24, 32, 48, 64, 96, 128), reps=5, flush=flush)
     del xs_tune
     ctxs, xs = [], []
     for sysr in reps:
@@ -293,9 +293,11 @@ def extra_workloads(args):
     def batched():
         b.nb_forces_batched(flags, xcat, fcat, e, w)
 
-    def plain():
-        for c, xr, fr, er, wr in zip(ctxs, xs, fs, es, ws):
-            c.nb_forces(flags, xr, fr, er, wr)
+    def plain_fn(cs):
+        def plain():
+            for c, xr, fr, er, wr in zip(cs, xs, fs, es, ws):
+                c.nb_forces(flags, xr, fr, er, wr)
+        return plain
 
     def time_fn(fn, reps_=20, warm=3):
         for _ in range(warm):
@@ -324,19 +326,34 @@ def extra_workloads(args):
         return g
 
     gb = graphed(batched)
-    gp = graphed(plain)
     t_batched_graph = time_fn(gb.replay)
-    t_plain_graph = time_fn(gp.replay)
-    t_plain_seq = time_fn(plain, reps_=5, warm=1)
     n_all = sum(c.n for c in ctxs)
+    del gb, b, ctxs
+    # the per-replica calls at the item size best for them (small systems alone want short items)
+    t_plain_graph, split_plain, ctxs_p = None, None, None
+    for sp in (8, 16, 32, 64):
+        cs = []
+        for sysr, xr in zip(reps, xs):
+            c = api.NbContext.from_system(sysr)
+            c.nb_set_split(sp)
+            c.build(xr, sysr.box)
+            cs.append(c)
+        gp = graphed(plain_fn(cs))
+        t = time_fn(gp.replay)
+        del gp
+        if t_plain_graph is None or t < t_plain_graph:
+            t_plain_graph, split_plain, ctxs_p = t, sp, cs
+        del cs
+    t_plain_seq = time_fn(plain_fn(ctxs_p), reps_=5, warm=1)
     out["batched_256_replicas"] = {
         "atoms_total": int(n_all), "replicas": R, "split_autotuned": int(tuned_b["split"]),
+        "split_plain_best": int(split_plain),
         "batched_graph_ms": t_batched_graph, "plain_graph_ms": t_plain_graph, "plain_sequential_ms": t_plain_seq,
         "system_evals_per_s_batched": R * 1e3 / t_batched_graph,
         "system_evals_per_s_plain_graph": R * 1e3 / t_plain_graph,
         "system_evals_per_s_plain_sequential": R * 1e3 / t_plain_seq,
     }
-    del gb, gp, b, ctxs, xs
+    del ctxs_p, xs
     # forward + adjoint on the 24k box with 6 LJ types
     s4 = synth.water_24k_types()
     c4 = api.NbContext.from_system(s4)
@@ -582,9 +599,51 @@ def main_reference(args):
 
 def main_profile(args):
     """A short, fixed launch sequence for profilers: one build, then force evaluations
-    (--profile-case forces) or PME + Ewald-correction calls (--profile-case pme)."""
+    (--profile-case forces: the 96k box; polymer_1.5m: the 1.5M-atom polymer/water box;
+    batched: one batched launch over the 256 replicas) or PME + Ewald-correction calls
+    (--profile-case pme)."""
     import torch
     from paper_2006_09167_gb300 import api, synth
+    flags = api.NB_ENERGY | api.NB_VIRIAL
+    if args.profile_case == "batched":
+        reps = synth.replica_set()
+        ctxs, xs = [], []
+        for sysr in reps:
+            c = api.NbContext.from_system(sysr)
+            c.nb_set_split(args.split or 64)
+            xr = torch.tensor(sysr.x, device="cuda")
+            c.build(xr, sysr.box)
+            ctxs.append(c)
+            xs.append(xr)
+        b = api.NbBatch(ctxs)
+        xcat = torch.cat(xs).contiguous()
+        fcat = torch.empty_like(xcat)
+        e = torch.empty(2 * len(ctxs), dtype=torch.float64, device="cuda")
+        w = torch.empty(9 * len(ctxs), dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            b.nb_forces_batched(flags, xcat, fcat, e, w)
+        torch.cuda.synchronize()
+        assert all(c.nb_get_error() == 0 for c in ctxs)
+        print(json.dumps({"profile_case": "spce_water_256_replicas_batched", "atoms": int(xcat.shape[0]),
+                          "calls": args.warmup + args.steps}))
+        return
+    if args.profile_case == "polymer_1.5m":
+        s = synth.polymer_water_box()
+        ctx = api.NbContext.from_system(s)
+        if args.split:
+            ctx.nb_set_split(args.split)
+        x = torch.tensor(s.x, device="cuda")
+        ctx.build(x, s.box)
+        f = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+        e = torch.empty(2, dtype=torch.float64, device="cuda")
+        w = torch.empty(9, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            ctx.nb_forces(flags, x, f, e, w)
+        torch.cuda.synchronize()
+        assert ctx.nb_get_error() == 0
+        print(json.dumps({"profile_case": "polymer_water_1.5m_ewald", "atoms": s.n,
+                          "launches": ctx.nb_get_stats()["n_launches"]}))
+        return
     s = synth.water_96k()
     ctx = api.NbContext.from_system(s)
     if args.profile_case == "pme":
@@ -628,7 +687,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true",
                     help="profiling target: warmup + steps force evaluations (energy+virial) of the 96k box only")
-    ap.add_argument("--profile-case", choices=["forces", "pme"], default="forces",
+    ap.add_argument("--profile-case", choices=["forces", "pme", "polymer_1.5m", "batched"], default="forces",
                     help="with --profile: the launch sequence to run")
     ap.add_argument("--split", type=int, default=0,
                     help="with --profile: the work-item split to build with (default: the library's)")

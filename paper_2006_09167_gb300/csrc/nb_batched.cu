@@ -3,9 +3,13 @@
 // The paper runs ensembles of independent simulations side by side on one GPU
 // to fill it (Sec. VI, Fig. 11) and fights kernel tails by ordering the work
 // longest first and splitting long lists (Sec. V.F).  Here the work items of
-// all systems form one queue, ordered longest first across systems; a
-// persistent grid (a few blocks per SM) lets each warp take the next item with
-// one atomic increment, so uneven system sizes do not leave SMs idle.  Each
+// all systems form one queue: system by system, each system's items longest
+// first, so the warps in flight touch a few systems at a time and their
+// positions and force accumulators stay in L2; only the globally shortest
+// items (two per resident warp) move to the end, longest first, so the launch
+// still ends on short items.  A persistent grid (a few blocks per SM) lets
+// each warp take the next item with one atomic increment, so uneven system
+// sizes do not leave SMs idle.  Each
 // item is evaluated by the same per-item code as the single-system kernel.
 // There are no waits between warps: the queue needs no device-side spinning.
 #include <algorithm>
@@ -210,10 +214,31 @@ nb_status nb_batch_create(nb_ctx *const *ctxs, int n, nb_batch **out) {
         nb_batch_destroy(b);
         return nb_cuda_status(err);
     }
-    // longest first across all systems; ties keep system order (stable)
-    std::stable_sort(items.begin(), items.end(), [](const It &a, const It &c) { return a.len > c.len; });
-    std::vector<int2> gmap(items.size());
-    for (size_t i = 0; i < items.size(); i++) gmap[i] = make_int2(items[i].r, items[i].item);
+    int dev = 0, sms = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) {
+        nb_batch_destroy(b);
+        return nb_cuda_status(err);
+    }
+    const int occ = b->coulomb == NB_COULOMB_RF      ? occupancy<NB_COULOMB_RF, true, true>()
+                    : b->coulomb == NB_COULOMB_EWALD ? occupancy<NB_COULOMB_EWALD, true, true>()
+                                                     : occupancy<NB_COULOMB_NONE, true, true>();
+    b->grid = std::max(1, std::min(sms * occ, ((int)items.size() + kBW - 1) / kBW));
+    // queue order: all but the shortest items in system order (each system's items are
+    // longest first in its list), then the shortest two per resident warp, longest first
+    const size_t n_tail = std::min(items.size(), (size_t)2 * b->grid * kBW);
+    std::vector<int> by_len(items.size());
+    for (size_t i = 0; i < items.size(); i++) by_len[i] = (int)i;
+    std::stable_sort(by_len.begin(), by_len.end(), [&](int a, int c) { return items[a].len > items[c].len; });
+    std::vector<char> in_tail(items.size(), 0);
+    for (size_t i = items.size() - n_tail; i < items.size(); i++) in_tail[by_len[i]] = 1;
+    std::vector<int2> gmap;
+    gmap.reserve(items.size());
+    for (size_t i = 0; i < items.size(); i++)
+        if (!in_tail[i]) gmap.push_back(make_int2(items[i].r, items[i].item));
+    for (size_t i = items.size() - n_tail; i < items.size(); i++)
+        gmap.push_back(make_int2(items[by_len[i]].r, items[by_len[i]].item));
     b->n_atoms = off;
     b->total_items = (int)items.size();
     b->n_gblk = (int)gblk.size();
@@ -229,17 +254,10 @@ nb_status nb_batch_create(nb_ctx *const *ctxs, int n, nb_batch **out) {
     up((void **)&b->gblk, gblk.data(), sizeof(int2) * gblk.size());
     up((void **)&b->ublk, ublk.data(), sizeof(int2) * ublk.size());
     if (err == cudaSuccess) err = cudaMalloc((void **)&b->queue, sizeof(int));
-    int dev = 0, sms = 0;
-    if (err == cudaSuccess) err = cudaGetDevice(&dev);
-    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) {
         nb_batch_destroy(b);
         return nb_cuda_status(err);
     }
-    int occ = b->coulomb == NB_COULOMB_RF      ? occupancy<NB_COULOMB_RF, true, true>()
-              : b->coulomb == NB_COULOMB_EWALD ? occupancy<NB_COULOMB_EWALD, true, true>()
-                                               : occupancy<NB_COULOMB_NONE, true, true>();
-    b->grid = std::max(1, std::min(sms * occ, (b->total_items + kBW - 1) / kBW));
     *out = b;
     return NB_OK;
 }
