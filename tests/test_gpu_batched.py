@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 from paper_2006_09167_gb300 import synth
-from helpers import TOL_F, energy_tolerances, rel, rms_rel
+from helpers import TOL_F, TOL_W, energy_tolerances, rel, rms_rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -82,6 +82,55 @@ def test_batched_oracle_parity_and_graph_replay(api, replicas):
         assert rms_rel(f[off[r]:off[r + 1]].cpu().numpy(), ref["F"]) < TOL_F
         assert rel(e[2 * r].item(), ref["E_lj"]) < tol_lj
         assert rel(e[2 * r + 1].item(), ref["E_c"]) < tol_c
+
+
+def test_batched_256_replicas_full_size(api):
+    """The full ensemble (256 uneven replicas, 4.75 M atoms) at the item size the
+    batched autotuner picks for it, one launch replayed in a CUDA graph: every
+    replica's forces, energies and virial against the FP64 cell-list oracle."""
+    reps = synth.replica_set()
+    ctxs, xs = [], []
+    for s in reps:
+        c = api.NbContext.from_system(s)
+        c.nb_set_split(128)
+        x = torch.tensor(s.x, device="cuda")
+        c.build(x, s.box)
+        ctxs.append(c)
+        xs.append(x)
+    b = api.NbBatch(ctxs)
+    R = len(ctxs)
+    xcat = torch.cat(xs).contiguous()
+    f = torch.empty_like(xcat)
+    e = torch.empty(2 * R, dtype=torch.float64, device="cuda")
+    w = torch.empty(9 * R, dtype=torch.float64, device="cuda")
+    flags = api.NB_ENERGY | api.NB_VIRIAL
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        b.nb_forces_batched(flags, xcat, f, e, w)
+    torch.cuda.current_stream().wait_stream(st)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.nb_forces_batched(flags, xcat, f, e, w)
+    f.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert all(c.nb_get_error() == 0 for c in ctxs)
+    off = b.offsets
+    fa, ea, wa = f.cpu().numpy(), e.cpu().numpy(), w.cpu().numpy()
+    worst = 0.0
+    for r, sysr in enumerate(reps):
+        ref = oracle.celllist(sysr)
+        tol_lj, tol_c = energy_tolerances(sysr, ref)
+        ef = rms_rel(fa[off[r]:off[r + 1]], ref["F"])
+        worst = max(worst, ef)
+        assert ef < TOL_F, (r, ef)
+        assert rel(ea[2 * r], ref["E_lj"]) < tol_lj, r
+        assert rel(ea[2 * r + 1], ref["E_c"]) < tol_c, r
+        wr = wa[9 * r:9 * r + 9].reshape(3, 3)
+        assert np.sqrt(((wr - ref["W"]) ** 2).sum() / (ref["W"] ** 2).sum()) < TOL_W, r
+    print(f"256 replicas: worst force RMS rel {worst:.2e}")
 
 
 def test_batch_requires_lists(api, replicas):
