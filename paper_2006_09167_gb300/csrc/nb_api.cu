@@ -87,6 +87,7 @@ nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     v.inner_len = c->inner_len;
     v.cj = c->cj_inner;
     v.masks = c->masks;
+    v.mask_lanes = c->mask_lanes;
     v.lj = c->lj;
     v.lje = c->lje;
     v.part = c->part;
@@ -289,6 +290,7 @@ void nb_destroy(nb_ctx *c) {
     dfree(c->cj_outer);
     dfree(c->cj_inner);
     dfree(c->masks);
+    dfree(c->mask_lanes);
     dfree(c->si_counts);
     dfree(c->si_offs);
     dfree(c->sort_tmp);
@@ -432,6 +434,7 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
     if (c->n_masks > c->masks_cap) {
         int cap = c->n_masks + c->n_masks / 8 + 16;
         if ((s = dalloc(&c->masks, (size_t)cap * 8)) != NB_OK) return s;
+        if ((s = dalloc(&c->mask_lanes, (size_t)cap * 32)) != NB_OK) return s;
         c->masks_cap = cap;
     }
     const int nblk = nb_force_blocks(c->n_items) + 1;

@@ -186,7 +186,7 @@ nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cu
     c->n_launches++;
     L2Prefetch pf;
     const bool lists = c->have_list;
-    const void *base[5] = {c->cj_inner, c->items, c->inner_len, c->type_s, c->masks};
+    const void *base[5] = {c->cj_inner, c->items, c->inner_len, c->type_s, c->mask_lanes};
     const long long bytes[5] = {lists ? (long long)c->n_j * 8 : 0, lists ? (long long)c->n_items * 16 : 0,
                                 lists ? (long long)c->n_items * 4 : 0, (long long)ns * 4,
                                 lists ? (long long)c->n_masks * 64 : 0};

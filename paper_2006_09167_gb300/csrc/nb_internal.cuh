@@ -13,6 +13,9 @@
 //   exclusion mask u64 per (i-cluster k, j-cluster): bit 8*a + b set = pair (i-atom a,
 //         j-atom b) interacts (cleared for excluded pairs, the lower triangle and padding
 //         of a self cluster pair).
+//   mask_lanes u16 [group][32 lanes]: the same bits in the pair kernels' lane order: lane
+//         (ti, tj) = (lane & 7, lane >> 3) holds at bit 2k + h the bit of pair (i-atom ti,
+//         j-atom tj + 4h) of i-cluster k.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -46,6 +49,7 @@ struct SysView {
     const int *inner_len;
     const int2 *cj;
     const unsigned long long *masks;
+    const unsigned short *mask_lanes;
     const float2 *lj;   // [T*T] (6*C6, 12*C12), symmetrised
     const float4 *lje;  // [T*T] (C6, C12, C12/rc^12 - C6/rc^6, 0), symmetrised
     float4 *f;          // sorted force accumulators
@@ -166,6 +170,7 @@ struct nb_ctx {
     int *inner_len = nullptr;
     int2 *cj_outer = nullptr, *cj_inner = nullptr, *cj_tmp = nullptr;
     unsigned long long *masks = nullptr;
+    unsigned short *mask_lanes = nullptr;  // [32 * masks_cap] the masks in lane order
     int *si_counts = nullptr;  // [3*si_cap]: j entries, items, mask groups per super-cluster
     int *si_offs = nullptr;    // [3*(si_cap+1)]
     int *sort_tmp = nullptr;   // item sort scratch

@@ -339,6 +339,8 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             xj1 = shift_j(xj1, sh);
         }
         const int tj0 = v.type[cj * NB_CL + tj], tj1 = v.type[cj * NB_CL + tj + 4];
+        // exclusion bits of the lane's two pairs for every i-cluster k (bits 2k, 2k + 1)
+        const unsigned mw = mg ? (unsigned)v.mask_lanes[(size_t)(mg - 1) * 32 + lane] : 0xffffu;
         // the lane's two j-atoms as packed pairs (component 0: tj, component 1: tj + 4)
         const float2 jx = make_float2(xj0.x, xj1.x), jy = make_float2(xj0.y, xj1.y);
         const float2 jz = make_float2(xj0.z, xj1.z), jq = make_float2(xj0.w, xj1.w);
@@ -351,12 +353,7 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
         while (both) {
             const int k = __ffs(both) - 1;
             both &= both - 1;
-            bool b0 = true, b1 = true;
-            if (mg) {
-                const unsigned long long m = v.masks[(size_t)(mg - 1) * 8 + k];
-                b0 = (m >> (ti * 8 + tj)) & 1ull;
-                b1 = (m >> (ti * 8 + tj + 4)) & 1ull;
-            }
+            const bool b0 = (mw >> (2 * k)) & 1u, b1 = (mw >> (2 * k + 1)) & 1u;
             const float4 xi = s_xi[k * NB_CL + ti];
             const int tio = s_ti[k * NB_CL + ti];
             const float2 dx = psub(p2(xi.x), jx), dy = psub(p2(xi.y), jy), dz = psub(p2(xi.z), jz);
@@ -386,12 +383,7 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             const int kb = __ffs(one) - 1;
             one &= one - 1;
             const bool ua = (hi >> ka) & 1, ub = (hi >> kb) & 1;  // warp-uniform
-            bool ba = true, bb = true;
-            if (mg) {
-                const unsigned long long* mm = v.masks + (size_t)(mg - 1) * 8;
-                ba = (mm[ka] >> (ti * 8 + tj + (ua ? 4 : 0))) & 1ull;
-                bb = (mm[kb] >> (ti * 8 + tj + (ub ? 4 : 0))) & 1ull;
-            }
+            const bool ba = (mw >> (2 * ka + (ua ? 1 : 0))) & 1u, bb = (mw >> (2 * kb + (ub ? 1 : 0))) & 1u;
             const float4 xia = s_xi[ka * NB_CL + ti], xib = s_xi[kb * NB_CL + ti];
             const float4 xja = ua ? xj1 : xj0, xjb = ub ? xj1 : xj0;
             const float2 dx = psub(make_float2(xia.x, xib.x), make_float2(xja.x, xjb.x));
@@ -431,11 +423,7 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
         if (one) {  // the last single-half i-cluster: one pair per lane
             const int k = __ffs(one) - 1;
             const bool upper = (hi >> k) & 1;  // warp-uniform
-            bool b = true;
-            if (mg) {
-                const unsigned long long m = v.masks[(size_t)(mg - 1) * 8 + k];
-                b = (m >> (ti * 8 + tj + (upper ? 4 : 0))) & 1ull;
-            }
+            const bool b = (mw >> (2 * k + (upper ? 1 : 0))) & 1u;
             const float4 xj = upper ? xj1 : xj0;
             const float4 xi = s_xi[k * NB_CL + ti];
             const int tio = s_ti[k * NB_CL + ti];

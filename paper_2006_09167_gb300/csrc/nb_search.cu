@@ -254,6 +254,27 @@ __global__ void k_scan4(int n, const int *__restrict__ cnt, int *__restrict__ of
 // ---- stable counting sort of items by length, longest first (Sec. V.F) ----
 constexpr int kSortBlock = 1024;
 
+// The exclusion masks again, in the order the pair kernels read them: word
+// (g, lane) holds, for lane (ti, tj) = (lane & 7, lane >> 3), the bits of the
+// lane's two pairs (i-atom ti with j-atoms tj and tj + 4) for each i-cluster k
+// of group g, at bits 2k and 2k + 1.  A warp then reads one 64-byte row per
+// entry instead of one 64-bit mask per i-cluster.
+__global__ void k_mask_lanes(long long n_words, const unsigned long long *__restrict__ masks,
+                             unsigned short *__restrict__ lanes) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_words) return;
+    const long long g = t >> 5;
+    const int lane = (int)(t & 31), ti = lane & 7, tj = lane >> 3;
+    unsigned w = 0;
+#pragma unroll
+    for (int k = 0; k < NB_SCL; k++) {
+        const unsigned long long m = masks[g * NB_SCL + k];
+        w |= (unsigned)((m >> (ti * 8 + tj)) & 1ull) << (2 * k);
+        w |= (unsigned)((m >> (ti * 8 + tj + 4)) & 1ull) << (2 * k + 1);
+    }
+    lanes[t] = (unsigned short)w;
+}
+
 __global__ void k_item_hist(int n, int split, const int4 *__restrict__ items, int *__restrict__ hist,
                             int nblk) {
     __shared__ int h[129];
@@ -359,6 +380,12 @@ nb_status nb_launch_search_write(nb_ctx *c, float rlist, cudaStream_t st) {
     c->n_launches++;
     k_search<true><<<nblk, kWarps * 32, 0, st>>>(a);
     NB_CUDA_TRY(cudaGetLastError());
+    if (c->n_masks > 0) {
+        const long long words = (long long)c->n_masks * 32;
+        c->n_launches++;
+        k_mask_lanes<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(words, c->masks, c->mask_lanes);
+        NB_CUDA_TRY(cudaGetLastError());
+    }
     // order items longest first (stable)
     int n = c->n_items;
     if (n > 0) {

@@ -153,18 +153,15 @@ __device__ __forceinline__ void vjp_item(const VjpView &v, int w, int nj, float4
         }
         const float4 gj0 = v.gf[cj * NB_CL + tj], gj1 = v.gf[cj * NB_CL + tj + 4];
         const int tb0 = sv.type[cj * NB_CL + tj], tb1 = sv.type[cj * NB_CL + tj + 4];
+        // exclusion bits of the lane's two pairs for every i-cluster k (bits 2k, 2k + 1)
+        const unsigned mw = mg ? (unsigned)sv.mask_lanes[(size_t)(mg - 1) * 32 + lane] : 0xffffu;
         float a0x = 0.f, a0y = 0.f, a0z = 0.f, a0q = 0.f, a1x = 0.f, a1y = 0.f, a1z = 0.f, a1q = 0.f;
         int both = lo & hi;
 #pragma unroll 1
         while (both) {
             const int k = __ffs(both) - 1;
             both &= both - 1;
-            bool b0 = true, b1 = true;
-            if (mg) {
-                const unsigned long long m = sv.masks[(size_t)(mg - 1) * 8 + k];
-                b0 = (m >> (ti * 8 + tj)) & 1ull;
-                b1 = (m >> (ti * 8 + tj + 4)) & 1ull;
-            }
+            const bool b0 = (mw >> (2 * k)) & 1u, b1 = (mw >> (2 * k + 1)) & 1u;
             const float4 xi = s_xi[k * NB_CL + ti];
             const float4 gi = s_gi[k * NB_CL + ti];
             const int ta = s_ti[k * NB_CL + ti];
@@ -198,11 +195,7 @@ __device__ __forceinline__ void vjp_item(const VjpView &v, int w, int nj, float4
             const int k = __ffs(one) - 1;
             one &= one - 1;
             const bool upper = (hi >> k) & 1;  // warp-uniform
-            bool b = true;
-            if (mg) {
-                const unsigned long long m = sv.masks[(size_t)(mg - 1) * 8 + k];
-                b = (m >> (ti * 8 + tj + (upper ? 4 : 0))) & 1ull;
-            }
+            const bool b = (mw >> (2 * k + (upper ? 1 : 0))) & 1u;
             const float4 xj = upper ? xj1 : xj0, gj = upper ? gj1 : gj0;
             const int tb = upper ? tb1 : tb0;
             const float4 xi = s_xi[k * NB_CL + ti];
