@@ -454,19 +454,6 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             elj.add(elj_e);
             ec.add(ec_e);
         }
-        if (VIR) {
-            const float ux = xj0.x - org.x, uy = xj0.y - org.y, uz = xj0.z - org.z;
-            const float wx = xj1.x - org.x, wy = xj1.y - org.y, wz = xj1.z - org.z;
-            vr[0] += ux * f0x + wx * f1x;
-            vr[1] += ux * f0y + wx * f1y;
-            vr[2] += ux * f0z + wx * f1z;
-            vr[3] += uy * f0x + wy * f1x;
-            vr[4] += uy * f0y + wy * f1y;
-            vr[5] += uy * f0z + wy * f1z;
-            vr[6] += uz * f0x + wz * f1x;
-            vr[7] += uz * f0y + wz * f1y;
-            vr[8] += uz * f0z + wz * f1z;
-        }
         // j-force reduction over the 8 i-lanes, transposed: partners ti and ti ^ 4
         // swap halves (lanes ti < 4 keep j-atom tj, lanes ti >= 4 keep tj + 4), then
         // a butterfly over the remaining 4 lanes sums one atom per lane group
@@ -481,7 +468,22 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             ky += __shfl_xor_sync(full, ky, o);
             kz += __shfl_xor_sync(full, kz, o);
         }
-        if ((ti & 3) == 0) atomicAdd(&v.f[cj * NB_CL + tj + (upper ? 4 : 0)], make_float4(kx, ky, kz, 0.f));
+        if ((ti & 3) == 0) {
+            atomicAdd(&v.f[cj * NB_CL + tj + (upper ? 4 : 0)], make_float4(kx, ky, kz, 0.f));
+            if (VIR) {  // the j-atom's share of sum r (x) F, from its reduced force
+                const float4 xj = upper ? xj1 : xj0;
+                const float ux = xj.x - org.x, uy = xj.y - org.y, uz = xj.z - org.z;
+                vr[0] += ux * kx;
+                vr[1] += ux * ky;
+                vr[2] += ux * kz;
+                vr[3] += uy * kx;
+                vr[4] += uy * ky;
+                vr[5] += uy * kz;
+                vr[6] += uz * kx;
+                vr[7] += uz * ky;
+                vr[8] += uz * kz;
+            }
+        }
     }
     __syncwarp();
 #pragma unroll

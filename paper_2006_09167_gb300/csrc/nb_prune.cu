@@ -60,9 +60,16 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunk
         const bool valid = e < e_end;
         const int2 ent = valid ? a.cj_outer[j0 + e] : make_int2(0, 0);
         const int im = ent.y & 0xff;
-        float4 xj[NB_CL];
+        // j-atoms b and b + 4 as packed pairs: component 0 decides the lower j-half,
+        // component 1 the upper (the force kernel's distances, rounded alike)
+        float2 jx[4], jy[4], jz[4];
 #pragma unroll
-        for (int b = 0; b < NB_CL; b++) xj[b] = shift_j(a.xq[ent.x * NB_CL + b], sh);
+        for (int b = 0; b < 4; b++) {
+            const float4 p0 = shift_j(a.xq[ent.x * NB_CL + b], sh), p1 = shift_j(a.xq[ent.x * NB_CL + b + 4], sh);
+            jx[b] = make_float2(p0.x, p1.x);
+            jy[b] = make_float2(p0.y, p1.y);
+            jz[b] = make_float2(p0.z, p1.z);
+        }
         int lo = 0, hi = 0;
 #pragma unroll
         for (int k = 0; k < NB_SCL; k++) {
@@ -70,11 +77,11 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunk
                 const float4 xi = s_xi[wib][k * NB_CL + t];
                 bool any0 = false, any1 = false;
 #pragma unroll
-                for (int b = 0; b < NB_CL; b++) {
-                    const float dx = xi.x - xj[b].x, dy = xi.y - xj[b].y, dz = xi.z - xj[b].z;
-                    const bool in = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < a.rin2;
-                    if (b < 4) any0 |= in;
-                    else any1 |= in;
+                for (int b = 0; b < 4; b++) {
+                    const float2 dx = psub(p2(xi.x), jx[b]), dy = psub(p2(xi.y), jy[b]), dz = psub(p2(xi.z), jz[b]);
+                    const float2 r2 = pfma(dz, dz, pfma(dy, dy, pmul(dx, dx)));
+                    any0 |= r2.x < a.rin2;
+                    any1 |= r2.y < a.rin2;
                 }
                 lo |= (int)any0 << k;
                 hi |= (int)any1 << k;
