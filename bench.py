@@ -42,7 +42,7 @@ N_PARTS = 2
 DT = 0.002  # ps
 
 # FP32 operations per effective pair interaction (inside rc) by flavour, counted
-# from the pair formulas ("Roofline"): distance 8, 1/r and powers 4,
+# from the pair formulas: distance 8, 1/r and powers 4,
 # LJ force 5, Coulomb force (Ewald rational 29 / reaction field 5), scalar sum 1,
 # force vector 3 and the i/j accumulation 6; energies add LJ 4, Coulomb (Ewald
 # exp*rational 16 / RF 8), accumulation 2; the virial adds 2 per pair (amortised).
