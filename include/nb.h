@@ -101,6 +101,7 @@ typedef struct {
 
 /* kernels timed by the tracer (nb_trace_read) */
 enum { NB_TRACE_FORCES = 0, NB_TRACE_PRUNE = 1, NB_TRACE_GATHER = 2, NB_TRACE_VJP = 3, NB_TRACE_KINDS = 4 };
+#define NB_TRACE_ALL ((1 << NB_TRACE_KINDS) - 1) /* nb_trace_enable: every kind */
 
 /* Create a context for one system (Sec. V.A: positions, box, types, charges,
  * exclusions and cut-offs define the problem).  q_host [N] charges, type_host
@@ -230,11 +231,15 @@ nb_status nb_set_fused_prune(nb_ctx *ctx, int on);
  * 16).  Takes effect at the next nb_pairlist_build. */
 nb_status nb_set_split(nb_ctx *ctx, int max_entries_per_item);
 
-/* Tracing (not in the paper): when enabled, CUDA events are recorded on the
- * launch stream around every force, prune, gather and adjoint kernel of this
- * context (at most 65536 launches between reads).  Enabling creates the events
- * (host resources); it is not allowed during stream capture. */
-nb_status nb_trace_enable(nb_ctx *ctx, int enable);
+/* Tracing (not in the paper): CUDA events are recorded on the launch stream
+ * around every kernel of the kinds selected by `kinds` (bit NB_TRACE_x set:
+ * kind x is traced; 0 turns tracing off; other bits: NB_ERR_INVALID_ARG) of
+ * this context, at most 65536 launches per kind between reads.  Each traced
+ * launch adds two event records to its stream, so a caller may trace a sample
+ * of launches by switching the selection between calls: launches traced so far
+ * stay pending until nb_trace_read returns them.  The first enabling creates
+ * the events (host resources); not allowed during stream capture. */
+nb_status nb_trace_enable(nb_ctx *ctx, int kinds);
 
 /* Device time of the traced launches of one kind since the last read:
  * *total_ms (sum of event intervals) and *n_launches.  Synchronises on the

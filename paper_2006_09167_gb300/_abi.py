@@ -44,6 +44,7 @@ NB_TRACE_FORCES = 0
 NB_TRACE_PRUNE = 1
 NB_TRACE_GATHER = 2
 NB_TRACE_VJP = 3
+NB_TRACE_KINDS = 4
 
 
 class NbParams(ctypes.Structure):

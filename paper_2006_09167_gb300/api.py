@@ -16,7 +16,8 @@ import torch
 
 from . import _abi
 from ._abi import (NB_COULOMB_EWALD, NB_COULOMB_NONE, NB_COULOMB_RF, NB_ENERGY, NB_LIST_INNER, NB_LIST_OUTER,  # noqa: F401
-                   NB_TRACE_FORCES, NB_TRACE_GATHER, NB_TRACE_PRUNE, NB_TRACE_VJP, NB_VIRIAL, NbError, check)
+                   NB_TRACE_FORCES, NB_TRACE_GATHER, NB_TRACE_KINDS, NB_TRACE_PRUNE, NB_TRACE_VJP, NB_VIRIAL, NbError,
+                   check)
 
 
 def _stream(stream: Optional[torch.cuda.Stream] = None) -> ctypes.c_void_p:
@@ -177,8 +178,13 @@ class NbContext:
     def nb_set_split(self, split: int):
         check(self._lib.nb_set_split(self.handle, int(split)), "nb_set_split")
 
-    def nb_trace_enable(self, enable: bool = True):
-        check(self._lib.nb_trace_enable(self.handle, 1 if enable else 0), "nb_trace_enable")
+    def nb_trace_enable(self, enable: bool = True, kinds=None):
+        """Time launches with CUDA events: every kind (kinds=None) or the listed
+        NB_TRACE_* kinds; enable=False turns tracing off."""
+        mask = 0
+        if enable:
+            mask = (1 << NB_TRACE_KINDS) - 1 if kinds is None else sum(1 << k for k in set(kinds))
+        check(self._lib.nb_trace_enable(self.handle, mask), "nb_trace_enable")
 
     def nb_trace_read(self, kind: int):
         """(total device ms, launches) of traced kernels of `kind` since the last read."""

@@ -98,7 +98,7 @@ def tune(system, x, velocities=None, *, splits: Sequence[int] = SPLITS, parts: S
         c = api.NbContext.from_system(system)
         c.nb_set_split(sp)
         c.build(x, system.box)
-        c.nb_trace_enable(True)
+        c.nb_trace_enable(True, kinds=[api.NB_TRACE_FORCES])
         for _ in range(3):
             c.nb_forces(flags, x, f, e, w)
         ctxs[sp] = c
@@ -118,7 +118,7 @@ def tune(system, x, velocities=None, *, splits: Sequence[int] = SPLITS, parts: S
     best_split = choose_split(split_ms)
     ctx = api.NbContext.from_system(system)
     ctx.nb_set_split(best_split)
-    ctx.nb_trace_enable(True)
+    ctx.nb_trace_enable(True, kinds=[api.NB_TRACE_FORCES, api.NB_TRACE_PRUNE])
     result = {"split": best_split, "split_ms": split_ms, "n_parts": 2, "missed": {}, "step_ms": {}}
     if velocities is not None:
         for npart in parts:

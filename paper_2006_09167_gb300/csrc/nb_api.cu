@@ -589,9 +589,10 @@ nb_status nb_get_stats(nb_ctx *c, nb_stats *o) {
     return NB_OK;
 }
 
-nb_status nb_trace_enable(nb_ctx *c, int enable) {
+nb_status nb_trace_enable(nb_ctx *c, int kinds) {
     if (!c) return NB_ERR_INVALID_ARG;
-    if (enable && c->ev_start[0].empty()) {
+    if (kinds & ~((1 << NB_TRACE_KINDS) - 1)) return NB_ERR_INVALID_ARG;
+    if (kinds && c->ev_start[0].empty()) {
         const int n = 65536;
         for (int k = 0; k < NB_TRACE_KINDS; k++) {
             c->ev_start[k].resize(n);
@@ -602,8 +603,7 @@ nb_status nb_trace_enable(nb_ctx *c, int enable) {
             }
         }
     }
-    c->trace = enable != 0;
-    for (int k = 0; k < NB_TRACE_KINDS; k++) c->ev_used[k] = 0;
+    c->trace_mask = (unsigned)kinds;
     return NB_OK;
 }
 

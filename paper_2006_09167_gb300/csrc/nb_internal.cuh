@@ -186,7 +186,7 @@ struct nb_ctx {
     int n_sm = 0;          // multiprocessors of the context's device
     long long n_launches = 0;
     // tracing: event pairs per traced kernel kind
-    bool trace = false;
+    unsigned trace_mask = 0;  // bit k: launches of trace kind k are timed
     std::vector<cudaEvent_t> ev_start[NB_TRACE_KINDS], ev_end[NB_TRACE_KINDS];
     int ev_used[NB_TRACE_KINDS] = {0, 0, 0, 0};
 };
@@ -198,7 +198,7 @@ struct NbTraceScope {
     cudaStream_t st;
     bool on;
     NbTraceScope(nb_ctx *c_, int kind_, cudaStream_t st_) : c(c_), kind(kind_), st(st_) {
-        on = c->trace && c->ev_used[kind] < (int)c->ev_start[kind].size();
+        on = ((c->trace_mask >> kind) & 1u) && c->ev_used[kind] < (int)c->ev_start[kind].size();
         if (on) cudaEventRecord(c->ev_start[kind][c->ev_used[kind]], st);
     }
     ~NbTraceScope() {

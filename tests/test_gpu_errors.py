@@ -118,3 +118,33 @@ def test_forces_are_reproducible(api):
     ctx.build(x, s.box)
     p2 = ctx.nb_debug_export_pairs(api.NB_LIST_OUTER)
     assert np.array_equal(np.sort(p1.view([("", p1.dtype)] * 5), axis=0), np.sort(p2.view([("", p2.dtype)] * 5), axis=0))
+
+
+def test_trace_selected_kinds(api):
+    """nb_trace_enable times only the kinds it is given; unknown kinds are rejected."""
+    s = synth.water_648()
+    ctx = api.NbContext.from_system(s)
+    x = torch.tensor(s.x, device="cuda")
+    f = torch.empty((s.n, 3), device="cuda")
+    ctx.build(x, s.box)
+    ctx.nb_trace_enable(True, kinds=[api.NB_TRACE_FORCES])
+    for k in range(3):
+        ctx.nb_forces(0, x, f)
+        ctx.nb_prune_rolling(k % 2, 2)
+    ms, n = ctx.nb_trace_read(api.NB_TRACE_FORCES)
+    assert n == 3 and ms > 0.0
+    assert ctx.nb_trace_read(api.NB_TRACE_PRUNE) == (0.0, 0)
+    assert ctx.nb_trace_read(api.NB_TRACE_GATHER) == (0.0, 0)
+    ctx.nb_trace_enable(True)  # every kind
+    ctx.nb_forces(0, x, f)
+    ctx.nb_prune_rolling(0, 2)
+    assert ctx.nb_trace_read(api.NB_TRACE_GATHER)[1] == 1
+    assert ctx.nb_trace_read(api.NB_TRACE_PRUNE)[1] == 1
+    # switching the selection keeps traced launches pending until they are read
+    ctx.nb_trace_enable(False)
+    ctx.nb_forces(0, x, f)
+    ctx.nb_trace_enable(True, kinds=[api.NB_TRACE_FORCES])
+    ctx.nb_forces(0, x, f)
+    assert ctx.nb_trace_read(api.NB_TRACE_FORCES)[1] == 2
+    assert ctx.nb_trace_read(api.NB_TRACE_FORCES) == (0.0, 0)
+    assert status_of(api, lambda: ctx.nb_trace_enable(True, kinds=[api.NB_TRACE_KINDS])) == 1
