@@ -57,6 +57,9 @@ FLOPS_PER_PAIR = {
 # 96k box from the ncu capture summarised in profiles/k_forces_spce_water_96k.md;
 # set to None whenever the force kernel changes until it is captured again.
 FORCE_KERNEL_DRAM_BYTES = 7620352
+# From the same capture: FP32 (FMA) pipe and issue-slot utilisation of that launch,
+# in percent of active cycles (what bounds the kernel; None with the bytes above).
+FORCE_KERNEL_NCU_PCT = {"fma_pipe_active": 52.3, "issue_slots_busy": 73.4}
 
 
 def rank_env():
@@ -579,6 +582,7 @@ def main_ours(args):
         "gpu_launches": int(res["launches"]),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": FORCE_KERNEL_DRAM_BYTES,
+                     "ncu_pct": FORCE_KERNEL_NCU_PCT,
                      "kernel": "k_forces<Ewald, energy, virial>", "avg_launch_ms": fk_avg_ms,
                      "timed_launches": int(res["fk_n"]),
                      "launch_timing": f"CUDA events around every {TRACE_EVERY}th force launch of the timed loop",
