@@ -644,8 +644,8 @@ def main_reference(args):
 def main_profile(args):
     """A short, fixed launch sequence for profilers: one build, then force evaluations
     (--profile-case forces: the 96k box; polymer_1.5m: the 1.5M-atom polymer/water box;
-    batched: one batched launch over the 256 replicas) or PME + Ewald-correction calls
-    (--profile-case pme)."""
+    batched: one batched launch over the 256 replicas; vjp: forward + adjoint calls on the
+    24k box with 6 LJ types) or PME + Ewald-correction calls (--profile-case pme)."""
     import torch
     from paper_2006_09167_gb300 import api, synth
     flags = api.NB_ENERGY | api.NB_VIRIAL
@@ -670,6 +670,26 @@ def main_profile(args):
         assert all(c.nb_get_error() == 0 for c in ctxs)
         print(json.dumps({"profile_case": "spce_water_256_replicas_batched", "atoms": int(xcat.shape[0]),
                           "calls": args.warmup + args.steps}))
+        return
+    if args.profile_case == "vjp":
+        s = synth.water_24k_types()
+        ctx = api.NbContext.from_system(s)
+        x = torch.tensor(s.x, device="cuda")
+        ctx.build(x, s.box)
+        T = s.n_types
+        gF = torch.randn((s.n, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(4))
+        gx, gq = torch.empty_like(x), torch.empty(s.n, device="cuda")
+        g6 = torch.empty((T, T), dtype=torch.float64, device="cuda")
+        g12 = torch.empty_like(g6)
+        f = torch.empty_like(x)
+        e = torch.empty(2, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            ctx.nb_forces(api.NB_ENERGY, x, f, e)
+            ctx.nb_forces_vjp(x, gF, 0.5, gx, gq, g6, g12)
+        torch.cuda.synchronize()
+        assert ctx.nb_get_error() == 0
+        print(json.dumps({"profile_case": "spce_water_24k_6types_forward_adjoint", "atoms": s.n,
+                          "launches": ctx.nb_get_stats()["n_launches"]}))
         return
     if args.profile_case == "polymer_1.5m":
         s = synth.polymer_water_box()
@@ -731,7 +751,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true",
                     help="profiling target: warmup + steps force evaluations (energy+virial) of the 96k box only")
-    ap.add_argument("--profile-case", choices=["forces", "pme", "polymer_1.5m", "batched"], default="forces",
+    ap.add_argument("--profile-case", choices=["forces", "pme", "polymer_1.5m", "batched", "vjp"], default="forces",
                     help="with --profile: the launch sequence to run")
     ap.add_argument("--split", type=int, default=0,
                     help="with --profile: the work-item split to build with (default: the library's)")

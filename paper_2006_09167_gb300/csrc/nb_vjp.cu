@@ -12,11 +12,13 @@
 // structure is the force kernel's: one warp per work item, lanes (ti, tj)
 // over the 8x8 cluster pair, i-gradients in registers, j-gradients reduced
 // over the ti lanes per j-entry.  Parameter gradients are accumulated in shared
-// memory (FP32, one item), then added to an FP64 table; the table is symmetrised
-// at the end so that a type pair a != b puts half of its gradient in [a][b] and
-// half in [b][a] (the pair parameter is (C[a][b] + C[b][a]) / 2).  With up to 8
-// atom types every lane owns a column of the accumulators ([type pair][33],
-// conflict-free) and the warp folds the columns once per item; with more types
+// memory per unordered type pair (FP32, one item), then added to an FP64 table;
+// the table is symmetrised at the end so that a type pair a != b puts half of its
+// gradient in [a][b] and half in [b][a] (the pair parameter is (C[a][b] +
+// C[b][a]) / 2).  With up to 8 atom types every lane owns a column of the
+// accumulators ([unordered type pair][33], conflict-free; T (T + 1) / 2 rows
+// instead of T^2 keep the shared memory of 4 warps low enough for 4 resident
+// blocks per SM up to 6 types) and the warp folds the columns once per item; with more types
 // the lanes add into one table per warp with shared-memory atomics.  (A few type
 // pairs shared by all 32 lanes serialise such atomics: on the 6-type 24k water box
 // they took two thirds of the kernel.)
@@ -51,7 +53,7 @@ struct VjpView {
 template <int COUL>
 __device__ __forceinline__ bool vjp_pair(const VjpView &v, const float4 *__restrict__ lje, float3 d, float3 wv,
                                          float qi, float qj, int tpair, bool bit, float3 &g, float &gqc, float &g6,
-                                         float &g12) {
+                                         float &g12, int &tsym) {
     const SysView &sv = v.s;
     const float f = sv.coul_f, gE = v.gE;
     float r2 = fmaf(d.z, d.z, fmaf(d.y, d.y, d.x * d.x));
@@ -64,7 +66,8 @@ __device__ __forceinline__ bool vjp_pair(const VjpView &v, const float4 *__restr
     const float rinv8 = rinv6 * rinv2;
     const float rinv12 = rinv6 * rinv6;
     const float rinv14 = rinv12 * rinv2;
-    const float4 le = lje[tpair];  // (C6, C12, shift, -)
+    const float4 le = lje[tpair];  // (C6, C12, shift, unordered type-pair index)
+    tsym = __float_as_int(le.w);
     const float phi_lj = fmaf(12.f * le.y, rinv14, -6.f * le.x * rinv8);
     const float dphi_lj = fmaf(-168.f * le.y, rinv14 * rinv2, 48.f * le.x * rinv8 * rinv2);
     const float qq = qi * qj;
@@ -167,12 +170,13 @@ __device__ __forceinline__ void vjp_item(const VjpView &v, int w, int nj, float4
             const int ta = s_ti[k * NB_CL + ti];
             float3 g0, g1;
             float q0, q1, c60, c61, c120, c121;
+            int u0, u1;
             const bool in0 = vjp_pair<COUL>(v, lje, make_float3(xi.x - xj0.x, xi.y - xj0.y, xi.z - xj0.z),
                                             make_float3(gi.x - gj0.x, gi.y - gj0.y, gi.z - gj0.z), xi.w, xj0.w,
-                                            ta * T + tb0, b0, g0, q0, c60, c120);
+                                            ta * T + tb0, b0, g0, q0, c60, c120, u0);
             const bool in1 = vjp_pair<COUL>(v, lje, make_float3(xi.x - xj1.x, xi.y - xj1.y, xi.z - xj1.z),
                                             make_float3(gi.x - gj1.x, gi.y - gj1.y, gi.z - gj1.z), xi.w, xj1.w,
-                                            ta * T + tb1, b1, g1, q1, c61, c121);
+                                            ta * T + tb1, b1, g1, q1, c61, c121, u1);
             float *ga = s_ga + k * 128 + lane;
             ga[0] += g0.x + g1.x;
             ga[32] += g0.y + g1.y;
@@ -186,8 +190,8 @@ __device__ __forceinline__ void vjp_item(const VjpView &v, int w, int nj, float4
             a1y -= g1.y;
             a1z -= g1.z;
             a1q = fmaf(xi.w, q1, a1q);
-            add_par<PRIV>(p6, p12, ta * T + tb0, lane, in0, c60, c120);
-            add_par<PRIV>(p6, p12, ta * T + tb1, lane, in1, c61, c121);
+            add_par<PRIV>(p6, p12, u0, lane, in0, c60, c120);
+            add_par<PRIV>(p6, p12, u1, lane, in1, c61, c121);
         }
         int one = lo ^ hi;
 #pragma unroll 1
@@ -203,9 +207,10 @@ __device__ __forceinline__ void vjp_item(const VjpView &v, int w, int nj, float4
             const int ta = s_ti[k * NB_CL + ti];
             float3 g;
             float q, c6, c12;
+            int u;
             const bool in = vjp_pair<COUL>(v, lje, make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z),
                                            make_float3(gi.x - gj.x, gi.y - gj.y, gi.z - gj.z), xi.w, xj.w, ta * T + tb,
-                                           b, g, q, c6, c12);
+                                           b, g, q, c6, c12, u);
             float *ga = s_ga + k * 128 + lane;
             ga[0] += g.x;
             ga[32] += g.y;
@@ -222,7 +227,7 @@ __device__ __forceinline__ void vjp_item(const VjpView &v, int w, int nj, float4
                 a0z -= g.z;
                 a0q = fmaf(xi.w, q, a0q);
             }
-            add_par<PRIV>(p6, p12, ta * T + tb, lane, in, c6, c12);
+            add_par<PRIV>(p6, p12, u, lane, in, c6, c12);
         }
         // j-gradients over the 8 i-lanes, transposed as in the force kernel
         const bool up = ti & 4;
@@ -272,21 +277,31 @@ __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v, int *queue) {
     __shared__ int s_ti[kVW][NB_SCA];
     __shared__ float s_ga[kVW][4 * NB_SCL * 32];
     __shared__ float4 s_lje[kVjpMaxT * kVjpMaxT];
-    extern __shared__ float s_par[];  // PRIV: [kVW][2][T*T][33]; else [kVW][2][T*T]
+    __shared__ int s_ord[kVjpMaxT * (kVjpMaxT + 1) / 2];
+    // parameter accumulators per unordered type pair {a, b} (a <= b), index
+    // u = a T - a (a - 1) / 2 + b - a; PRIV: [kVW][2][TS][33]; else [kVW][2][TS]
+    extern __shared__ float s_par[];
     const SysView &sv = v.s;
-    const int T = sv.T, TT = T * T;
-    for (int t = threadIdx.x; t < TT; t += blockDim.x) s_lje[t] = sv.lje[t];
+    const int T = sv.T, TT = T * T, TS = T * (T + 1) / 2;
+    for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+        const int a = min(t / T, t % T), b = max(t / T, t % T);
+        const int u = a * T - a * (a - 1) / 2 + b - a;
+        float4 le = sv.lje[t];
+        le.w = __int_as_float(u);  // the pair's accumulator, read with its parameters
+        s_lje[t] = le;
+        if (a == t / T) s_ord[u] = t;  // a <= b: the slot gpar[a T + b] receives the pair's total
+    }
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
-    float *const p6 = s_par + (size_t)wib * 2 * TT * (PRIV ? kColStride : 1);
-    float *const p12 = p6 + TT * (PRIV ? kColStride : 1);
+    float *const p6 = s_par + (size_t)wib * 2 * TS * (PRIV ? kColStride : 1);
+    float *const p12 = p6 + TS * (PRIV ? kColStride : 1);
     if (PRIV) {
-        for (int t = 0; t < TT; t++) {
+        for (int t = 0; t < TS; t++) {
             p6[t * kColStride + lane] = 0.f;
             p12[t * kColStride + lane] = 0.f;
         }
     } else {
-        for (int t = lane; t < TT; t += 32) {
+        for (int t = lane; t < TS; t += 32) {
             p6[t] = 0.f;
             p12[t] = 0.f;
         }
@@ -299,7 +314,7 @@ __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v, int *queue) {
         if (nj > 0) {
             vjp_item<COUL, PRIV>(v, w, nj, s_xi[wib], s_gi[wib], s_ti[wib], s_ga[wib], s_lje, p6, p12, T);
             __syncwarp();
-            for (int t = lane; t < TT; t += 32) {
+            for (int t = lane; t < TS; t += 32) {
                 float a = 0.f, b = 0.f;
                 if (PRIV) {  // lane t folds row t over the 32 lane columns (banks (t + l) mod 32), then clears it
                     for (int l = 0; l < 32; l++) {
@@ -314,8 +329,10 @@ __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v, int *queue) {
                     p6[t] = 0.f;
                     p12[t] = 0.f;
                 }
-                if (a != 0.f) atomicAdd(&v.gpar[t], (double)a);
-                if (b != 0.f) atomicAdd(&v.gpar[TT + t], (double)b);
+                // the total of the unordered pair into one ordered slot; the finish kernel
+                // symmetrises (gpar[a T + b] + gpar[b T + a]) / 2
+                if (a != 0.f) atomicAdd(&v.gpar[s_ord[t]], (double)a);
+                if (b != 0.f) atomicAdd(&v.gpar[TT + s_ord[t]], (double)b);
             }
         }
         __syncwarp();  // the staging arrays and accumulators are reused by the next item
@@ -420,9 +437,9 @@ nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, f
         NbTraceScope tr(c, NB_TRACE_VJP, st);
         c->n_launches++;
         const int nb = (v.s.n_items + kVW - 1) / kVW;
-        const int TT = c->T * c->T;
+        const int TS = c->T * (c->T + 1) / 2;
         if (c->T <= kVjpPrivMaxT) {
-            const size_t smem = sizeof(float) * kVW * 2 * TT * kColStride;
+            const size_t smem = sizeof(float) * kVW * 2 * TS * kColStride;
             if (c->coulomb == NB_COULOMB_RF)
                 launch_vjp<NB_COULOMB_RF, true>(v, nb, smem, c->n_sm, c->queue, st);
             else if (c->coulomb == NB_COULOMB_EWALD)
@@ -430,7 +447,7 @@ nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, f
             else
                 launch_vjp<NB_COULOMB_NONE, true>(v, nb, smem, c->n_sm, c->queue, st);
         } else {
-            const size_t smem = sizeof(float) * kVW * 2 * TT;
+            const size_t smem = sizeof(float) * kVW * 2 * TS;
             if (c->coulomb == NB_COULOMB_RF)
                 launch_vjp<NB_COULOMB_RF, false>(v, nb, smem, c->n_sm, c->queue, st);
             else if (c->coulomb == NB_COULOMB_EWALD)
