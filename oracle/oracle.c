@@ -300,14 +300,19 @@ int or_celllist(int n, const double *x, const double *q, const int *type, int T,
 
 /* ------------------------------------------------------ explicit image-pair set */
 /* pairs: [npairs][5] = (i, j, sx, sy, sz); the pair vector is x_i - x_j + s*L
- * (s integer per axis, no minimum image).  Pairs with r >= rc contribute nothing.
+ * (s integer per axis, no minimum image).  Pairs with r >= rc contribute nothing,
+ * unless `frozen` is set: then every listed pair is summed at its distance.
  * Every listed pair is summed as given (exclusions are not re-applied). */
 int or_listset(int n, const double *x, const double *q, const int *type, int T, const double *c6,
                const double *c12, const double *box, int coulomb, double eps_r, double eps_rf,
-               double beta, double rc, int64_t npairs, const int64_t *pairs, double *F, double *E,
-               double *W, int64_t *n_in) {
+               double beta, double rc, int64_t npairs, const int64_t *pairs, int frozen, double *F,
+               double *E, double *W, int64_t *n_in) {
     setup_t s;
     make_setup(&s, coulomb, eps_r, eps_rf, beta, rc, T, c6, c12);
+    /* frozen: every listed pair is summed whatever its distance (the pair set is held
+     * fixed, as for finite differences of a frozen list); the potentials keep their
+     * shift at rc and continue smoothly beyond it */
+    const double rtest2 = frozen ? INFINITY : s.rc2;
     memset(F, 0, sizeof(double) * 3 * (size_t)n);
     double elj = 0, ec = 0, w[9] = {0};
     int64_t cnt = 0;
@@ -318,7 +323,7 @@ int or_listset(int n, const double *x, const double *q, const int *type, int T, 
         double d[3];
         for (int k = 0; k < 3; k++) d[k] = x[3 * i + k] - x[3 * j + k] + (double)e[2 + k] * box[k];
         double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        if (!(r2 < s.rc2)) continue;
+        if (!(r2 < rtest2)) continue;
         pair_t pt;
         pair_terms(&s, r2, q[i] * q[j], pair_c(c6, T, type[i], type[j]), pair_c(c12, T, type[i], type[j]), 0,
                    &pt);

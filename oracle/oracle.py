@@ -45,7 +45,7 @@ def _load():
                                               ctypes.c_int, _i, _d, _d, _d, _l]
         _lib.or_listset.argtypes = common + [_d, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_int64, _l,
-                                             _d, _d, _d, _l]
+                                             ctypes.c_int, _d, _d, _d, _l]
         _lib.or_pairs_within.argtypes = [ctypes.c_int, _d, _d, _i, _i, ctypes.c_double,
                                          ctypes.c_int64, _l]
         _lib.or_pairs_within.restype = ctypes.c_int64
@@ -141,8 +141,12 @@ def celllist(s, x=None, subset=None):
     return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=npairs.value)
 
 
-def listset(s, pairs, x=None):
-    """Sum exactly the given image pairs [(i, j, sx, sy, sz)] that lie inside rc."""
+def listset(s, pairs, x=None, frozen=False):
+    """Sum exactly the given image pairs [(i, j, sx, sy, sz)] that lie inside rc.
+
+    frozen=True sums every given pair whatever its distance (a frozen pair set: the
+    shifted potentials continue smoothly beyond rc), so that finite differences of
+    the result are those of a fixed list even where a step moves a pair across rc."""
     lib = _load()
     xx, q, ty, c6, c12, off, idx, box = _arrays(s)
     if x is not None:
@@ -160,7 +164,7 @@ def listset(s, pairs, x=None):
     n_in = ctypes.c_int64(0)
     co, er, erf_, be = _coul(s)
     rc = lib.or_listset(n, _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d), _p(c12, _d),
-                        _p(box, _d), co, er, erf_, be, float(s.rc), npair, _p(pr, _l), _p(F, _d),
+                        _p(box, _d), co, er, erf_, be, float(s.rc), npair, _p(pr, _l), int(bool(frozen)), _p(F, _d),
                         _p(E, _d), _p(W, _d), ctypes.byref(n_in))
     if rc != 0:
         raise ValueError("oracle: pair index out of range")
