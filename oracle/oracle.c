@@ -24,13 +24,17 @@
  *   f = 138.935458 / eps_r  kJ mol^-1 nm e^-2
  * The pair parameters of atoms with types a, b are C = (C[a][b] + C[b][a]) / 2
  * (the table entry itself for the symmetric tables callers pass).
- * Forces F_i = -dE/dx_i = sum_j phi(r) r_vec, phi = -(1/r) dV/dr, r_vec = x_i - x_j (image).
+ * Forces F_i = -dE/dx_i = sum_j phi(r) r_vec, phi = -(1/r) dV/dr, r_vec = x_i - x_j (image);
+ * optionally also Fabs_i = sum_j |phi(r) r_vec|, the size of the terms F_i is the sum of
+ * (tests scale the FP32 accumulation error of a force by it).
  * Virial W = -1/2 sum_pairs r_vec (x) F_ij (3x3).
  *
  * Pieces: brute force O(N^2) (or_brute), its own cubic cell list (or_celllist,
  * optionally restricted to a subset of atoms), an evaluator over an explicit
  * set of image pairs (or_listset), the brute-force pair set within a radius
- * (or_pairs_within) and the analytic vector-Jacobian product (or_vjp).
+ * (or_pairs_within), the analytic vector-Jacobian product (or_vjp), and sums
+ * over the pairs that tests use to size FP32 rounding bounds (or_energy_moments,
+ * or_energy_hist).
  */
 #include <math.h>
 #include <stdint.h>
@@ -135,12 +139,13 @@ static inline void min_image(const double *xi, const double *xj, const double *b
 int or_brute(int n, const double *x, const double *q, const int *type, int T, const double *c6,
              const double *c12, const int *excl_off, const int *excl_idx, const double *box,
              int coulomb, double eps_r, double eps_rf, double beta, double rc,
-             double *F, double *E, double *W, int64_t *npairs) {
+             double *F, double *E, double *W, int64_t *npairs, double *Fabs) {
     setup_t s;
     make_setup(&s, coulomb, eps_r, eps_rf, beta, rc, T, c6, c12);
     for (int k = 0; k < 3; k++)
         if (!(rc < 0.5 * box[k])) return 1;
     memset(F, 0, sizeof(double) * 3 * (size_t)n);
+    if (Fabs) memset(Fabs, 0, sizeof(double) * (size_t)n);
     double elj = 0.0, ec = 0.0, w[9] = {0};
     int64_t np = 0;
     for (int i = 0; i < n; i++) {
@@ -157,6 +162,10 @@ int or_brute(int n, const double *x, const double *q, const int *type, int T, co
             for (int k = 0; k < 3; k++) {
                 F[3 * i + k] += phi * d[k];
                 F[3 * j + k] -= phi * d[k];
+            }
+            if (Fabs) {
+                Fabs[i] += fabs(phi) * sqrt(r2);
+                Fabs[j] += fabs(phi) * sqrt(r2);
             }
             for (int a = 0; a < 3; a++)
                 for (int b = 0; b < 3; b++) w[3 * a + b] += -0.5 * d[a] * phi * d[b];
@@ -227,7 +236,7 @@ static void free_cells(cells_t *c) {
 int or_celllist(int n, const double *x, const double *q, const int *type, int T, const double *c6,
                 const double *c12, const int *excl_off, const int *excl_idx, const double *box,
                 int coulomb, double eps_r, double eps_rf, double beta, double rc, int nsub,
-                const int *sub, double *F, double *E, double *W, int64_t *npairs) {
+                const int *sub, double *F, double *E, double *W, int64_t *npairs, double *Fabs) {
     setup_t s;
     make_setup(&s, coulomb, eps_r, eps_rf, beta, rc, T, c6, c12);
     for (int k = 0; k < 3; k++)
@@ -236,7 +245,7 @@ int or_celllist(int n, const double *x, const double *q, const int *type, int T,
     if (!build_cells(&c, n, x, box, rc)) {
         if (sub != NULL) return 2;
         return or_brute(n, x, q, type, T, c6, c12, excl_off, excl_idx, box, coulomb, eps_r, eps_rf,
-                        beta, rc, F, E, W, npairs);
+                        beta, rc, F, E, W, npairs, Fabs);
     }
     int m = sub ? nsub : n;
     double *e_at = (double *)calloc((size_t)m * 2, sizeof(double));
@@ -247,7 +256,7 @@ int or_celllist(int n, const double *x, const double *q, const int *type, int T,
         int i = sub ? sub[t] : t;
         int ci[3];
         cell_of(&c, x + 3 * i, box, ci);
-        double fi[3] = {0, 0, 0};
+        double fi[3] = {0, 0, 0}, fa = 0.0;
         for (int dx = -1; dx <= 1; dx++)
             for (int dy = -1; dy <= 1; dy++)
                 for (int dz = -1; dz <= 1; dz++) {
@@ -268,6 +277,7 @@ int or_celllist(int n, const double *x, const double *q, const int *type, int T,
                                    pair_c(c12, T, type[i], type[j]), 0, &pt);
                         double phi = pt.plj + pt.pc;
                         for (int k = 0; k < 3; k++) fi[k] += phi * d[k];
+                        fa += fabs(phi) * sqrt(r2);
                         e_at[2 * t] += 0.5 * pt.vlj;
                         e_at[2 * t + 1] += 0.5 * pt.vc;
                         for (int u = 0; u < 3; u++)
@@ -276,6 +286,7 @@ int or_celllist(int n, const double *x, const double *q, const int *type, int T,
                     }
                 }
         for (int k = 0; k < 3; k++) F[3 * t + k] = fi[k];
+        if (Fabs) Fabs[t] = fa;
     }
     if (sub == NULL) {
         double elj = 0, ec = 0, w[9] = {0};
@@ -306,7 +317,7 @@ int or_celllist(int n, const double *x, const double *q, const int *type, int T,
 int or_listset(int n, const double *x, const double *q, const int *type, int T, const double *c6,
                const double *c12, const double *box, int coulomb, double eps_r, double eps_rf,
                double beta, double rc, int64_t npairs, const int64_t *pairs, int frozen, double *F,
-               double *E, double *W, int64_t *n_in) {
+               double *E, double *W, int64_t *n_in, double *Fabs) {
     setup_t s;
     make_setup(&s, coulomb, eps_r, eps_rf, beta, rc, T, c6, c12);
     /* frozen: every listed pair is summed whatever its distance (the pair set is held
@@ -314,6 +325,7 @@ int or_listset(int n, const double *x, const double *q, const int *type, int T, 
      * shift at rc and continue smoothly beyond it */
     const double rtest2 = frozen ? INFINITY : s.rc2;
     memset(F, 0, sizeof(double) * 3 * (size_t)n);
+    if (Fabs) memset(Fabs, 0, sizeof(double) * (size_t)n);
     double elj = 0, ec = 0, w[9] = {0};
     int64_t cnt = 0;
     for (int64_t p = 0; p < npairs; p++) {
@@ -331,6 +343,10 @@ int or_listset(int n, const double *x, const double *q, const int *type, int T, 
         for (int k = 0; k < 3; k++) {
             F[3 * i + k] += phi * d[k];
             F[3 * j + k] -= phi * d[k];
+        }
+        if (Fabs) {
+            Fabs[i] += fabs(phi) * sqrt(r2);
+            Fabs[j] += fabs(phi) * sqrt(r2);
         }
         for (int a = 0; a < 3; a++)
             for (int b = 0; b < 3; b++) w[3 * a + b] += -0.5 * d[a] * phi * d[b];
@@ -501,6 +517,83 @@ int or_energy_moments(int n, const double *x, const double *q, const int *type, 
     m[0] = m[1] = m[2] = m[3] = 0.0;
     for (int i = 0; i < n; i++)
         for (int k = 0; k < 4; k++) m[k] += acc[4 * i + k];
+    free(acc);
+    if (use_cells) free_cells(&c);
+    return 0;
+}
+
+/* Radial histogram of the pair terms inside rc: for nbins equal bins of r on
+ * [0, rc), h[6*k + 0..5] = number of pairs, sum of qi qj, sum of V_LJ, sum of
+ * V_LJ^2, sum of V_C, sum of V_C^2 over the pairs whose distance falls in bin k.
+ * The bins add up to the energies of or_celllist.  Tests combine them with a
+ * model of FP32 rounding per distance to bound the error of an FP32 energy sum. */
+int or_energy_hist(int n, const double *x, const double *q, const int *type, int T, const double *c6,
+                   const double *c12, const int *excl_off, const int *excl_idx, const double *box, int coulomb,
+                   double eps_r, double eps_rf, double beta, double rc, int nbins, double *h) {
+    setup_t s;
+    make_setup(&s, coulomb, eps_r, eps_rf, beta, rc, T, c6, c12);
+    for (int k = 0; k < 3; k++)
+        if (!(rc < 0.5 * box[k])) return 1;
+    if (nbins < 1) return 2;
+    cells_t c;
+    int use_cells = build_cells(&c, n, x, box, rc);
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    double *acc = (double *)calloc((size_t)nt * nbins * 6, sizeof(double));
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *ht = acc + (size_t)tid * nbins * 6;
+#pragma omp for schedule(dynamic, 64)
+        for (int i = 0; i < n; i++) {
+            int ci[3] = {0, 0, 0};
+            if (use_cells) cell_of(&c, x + 3 * i, box, ci);
+            int span = use_cells ? 1 : 0;
+            for (int dx = -span; dx <= span; dx++)
+                for (int dy = -span; dy <= span; dy++)
+                    for (int dz = -span; dz <= span; dz++) {
+                        int lo = 0, hi = n;
+                        if (use_cells) {
+                            int a = (ci[0] + dx + c.nc[0]) % c.nc[0];
+                            int b = (ci[1] + dy + c.nc[1]) % c.nc[1];
+                            int e = (ci[2] + dz + c.nc[2]) % c.nc[2];
+                            int cc = (a * c.nc[1] + b) * c.nc[2] + e;
+                            lo = c.head[cc];
+                            hi = c.head[cc + 1];
+                        }
+                        for (int p = lo; p < hi; p++) {
+                            int j = use_cells ? c.atoms[p] : p;
+                            if (j <= i) continue; /* each unordered pair once */
+                            double d[3];
+                            min_image(x + 3 * i, x + 3 * j, box, d);
+                            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                            if (!(r2 < s.rc2)) continue;
+                            if (excluded(excl_off, excl_idx, i, j)) continue;
+                            pair_t pt;
+                            double qq = q[i] * q[j];
+                            pair_terms(&s, r2, qq, pair_c(c6, T, type[i], type[j]), pair_c(c12, T, type[i], type[j]),
+                                       0, &pt);
+                            int k = (int)(sqrt(r2) / rc * nbins);
+                            if (k >= nbins) k = nbins - 1;
+                            double *b = ht + 6 * k;
+                            b[0] += 1.0;
+                            b[1] += qq;
+                            b[2] += pt.vlj;
+                            b[3] += pt.vlj * pt.vlj;
+                            b[4] += pt.vc;
+                            b[5] += pt.vc * pt.vc;
+                        }
+                    }
+        }
+    }
+    memset(h, 0, sizeof(double) * 6 * (size_t)nbins);
+    for (int t = 0; t < nt; t++)
+        for (int k = 0; k < 6 * nbins; k++) h[k] += acc[(size_t)t * nbins * 6 + k];
     free(acc);
     if (use_cells) free_cells(&c);
     return 0;

@@ -39,13 +39,13 @@ def _load():
         _lib = ctypes.CDLL(build())
         common = [ctypes.c_int, _d, _d, _i, ctypes.c_int, _d, _d]
         _lib.or_brute.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                           ctypes.c_double, ctypes.c_double, _d, _d, _d, _l]
+                                           ctypes.c_double, ctypes.c_double, _d, _d, _d, _l, _d]
         _lib.or_celllist.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                              ctypes.c_int, _i, _d, _d, _d, _l]
+                                              ctypes.c_int, _i, _d, _d, _d, _l, _d]
         _lib.or_listset.argtypes = common + [_d, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_int64, _l,
-                                             ctypes.c_int, _d, _d, _d, _l]
+                                             ctypes.c_int, _d, _d, _d, _l, _d]
         _lib.or_pairs_within.argtypes = [ctypes.c_int, _d, _d, _i, _i, ctypes.c_double,
                                          ctypes.c_int64, _l]
         _lib.or_pairs_within.restype = ctypes.c_int64
@@ -54,6 +54,9 @@ def _load():
                                          _d, _d, _d]
         _lib.or_energy_moments.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double,
                                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _d]
+        _lib.or_energy_hist.argtypes = common + [_i, _i, _d, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                 _d]
         _lib.or_ewald_recip.argtypes = [ctypes.c_int, _d, _d, _d, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, _d, _d]
         _lib.or_ewald_excl.argtypes = [ctypes.c_int, _d, _d, _d, _i, _i, ctypes.c_double, ctypes.c_double,
@@ -90,7 +93,8 @@ def _coul(s):
 
 
 def brute(s, x=None):
-    """O(N^2) evaluation. Returns dict(F [N,3], E_lj, E_c, W [3,3], npairs)."""
+    """O(N^2) evaluation. Returns dict(F [N,3], E_lj, E_c, W [3,3], npairs, Fabs [N]);
+    Fabs[i] is the sum over atom i's pairs of the magnitude of the pair force."""
     lib = _load()
     xx, q, ty, c6, c12, off, idx, box = _arrays(s)
     if x is not None:
@@ -100,17 +104,19 @@ def brute(s, x=None):
     E = np.zeros(2)
     W = np.zeros(9)
     npairs = ctypes.c_int64(0)
+    Fabs = np.zeros(n)
     co, er, erf_, be = _coul(s)
     rc = lib.or_brute(n, _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d), _p(c12, _d),
                       _p(off, _i), _p(idx, _i), _p(box, _d), co, er, erf_, be, float(s.rc),
-                      _p(F, _d), _p(E, _d), _p(W, _d), ctypes.byref(npairs))
+                      _p(F, _d), _p(E, _d), _p(W, _d), ctypes.byref(npairs), _p(Fabs, _d))
     if rc != 0:
         raise ValueError("oracle: rc must be < L/2")
-    return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=npairs.value)
+    return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=npairs.value, Fabs=Fabs)
 
 
 def celllist(s, x=None, subset=None):
-    """Cell-list evaluation (all cores).  With subset: forces on those atoms only."""
+    """Cell-list evaluation (all cores), the keys of brute().  With subset: forces (F, Fabs)
+    on those atoms only."""
     lib = _load()
     xx, q, ty, c6, c12, off, idx, box = _arrays(s)
     if x is not None:
@@ -120,25 +126,27 @@ def celllist(s, x=None, subset=None):
     if subset is not None:
         sub = np.ascontiguousarray(subset, dtype=np.int32)
         F = np.zeros((sub.size, 3))
+        Fabs = np.zeros(sub.size)
         E = np.zeros(2)
         W = np.zeros(9)
         rc = lib.or_celllist(n, _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d),
                              _p(c12, _d), _p(off, _i), _p(idx, _i), _p(box, _d), co, er, erf_, be,
                              float(s.rc), sub.size, _p(sub, _i), _p(F, _d), _p(E, _d), _p(W, _d),
-                             None)
+                             None, _p(Fabs, _d))
         if rc != 0:
             raise ValueError("oracle: subset evaluation needs >= 3 cells per axis and rc < L/2")
-        return dict(F=F)
+        return dict(F=F, Fabs=Fabs)
     F = np.zeros((n, 3))
+    Fabs = np.zeros(n)
     E = np.zeros(2)
     W = np.zeros(9)
     npairs = ctypes.c_int64(0)
     rc = lib.or_celllist(n, _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d), _p(c12, _d),
                          _p(off, _i), _p(idx, _i), _p(box, _d), co, er, erf_, be, float(s.rc), 0,
-                         None, _p(F, _d), _p(E, _d), _p(W, _d), ctypes.byref(npairs))
+                         None, _p(F, _d), _p(E, _d), _p(W, _d), ctypes.byref(npairs), _p(Fabs, _d))
     if rc != 0:
         raise ValueError("oracle: rc must be < L/2")
-    return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=npairs.value)
+    return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=npairs.value, Fabs=Fabs)
 
 
 def listset(s, pairs, x=None, frozen=False):
@@ -159,16 +167,17 @@ def listset(s, pairs, x=None, frozen=False):
         npair = pr.shape[0]
     n = xx.shape[0]
     F = np.zeros((n, 3))
+    Fabs = np.zeros(n)
     E = np.zeros(2)
     W = np.zeros(9)
     n_in = ctypes.c_int64(0)
     co, er, erf_, be = _coul(s)
     rc = lib.or_listset(n, _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d), _p(c12, _d),
                         _p(box, _d), co, er, erf_, be, float(s.rc), npair, _p(pr, _l), int(bool(frozen)), _p(F, _d),
-                        _p(E, _d), _p(W, _d), ctypes.byref(n_in))
+                        _p(E, _d), _p(W, _d), ctypes.byref(n_in), _p(Fabs, _d))
     if rc != 0:
         raise ValueError("oracle: pair index out of range")
-    return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=n_in.value)
+    return dict(F=F, E_lj=E[0], E_c=E[1], W=W.reshape(3, 3), npairs=n_in.value, Fabs=Fabs)
 
 
 def pairs_within(s, rcut, x=None):
@@ -227,6 +236,23 @@ def energy_moments(s, x=None, with_abs=False):
     if with_abs:
         return float(m[0]), float(m[1]), float(m[2]), float(m[3])
     return float(m[0]), float(m[1])
+
+
+def energy_hist(s, nbins, x=None):
+    """Radial histogram of the pair terms inside rc (nbins equal bins of r on [0, rc)):
+    float64 [nbins, 6] with columns (pairs, sum qi qj, sum V_LJ, sum V_LJ^2, sum V_C, sum V_C^2)."""
+    lib = _load()
+    xx, q, ty, c6, c12, off, idx, box = _arrays(s)
+    if x is not None:
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+    h = np.zeros((int(nbins), 6))
+    co, er, erf_, be = _coul(s)
+    rc = lib.or_energy_hist(xx.shape[0], _p(xx, _d), _p(q, _d), _p(ty, _i), c6.shape[0], _p(c6, _d), _p(c12, _d),
+                            _p(off, _i), _p(idx, _i), _p(box, _d), co, er, erf_, be, float(s.rc), int(nbins),
+                            _p(h, _d))
+    if rc != 0:
+        raise ValueError("oracle: rc must be < L/2 and nbins >= 1")
+    return h
 
 
 def num_threads() -> int:

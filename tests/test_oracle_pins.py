@@ -372,3 +372,85 @@ def test_energy_moments_are_squared_radial_derivatives():
         d_c = r * (op["E_c"] - om["E_c"]) / (2 * h)
         assert m_lj == pytest.approx(d_lj ** 2, rel=1e-6)
         assert m_c == pytest.approx(d_c ** 2, rel=1e-6)
+
+
+def _three_atoms(coulomb, beta):
+    # three atoms on a line: pair energies of both signs (LJ attractive and repulsive
+    # pairs, Coulomb like and unlike charges)
+    c6, c12 = synth.lj_c6_c12(0.34, 0.8)
+    return make_sys([[1.0, 1.0, 1.0], [1.33, 1.0, 1.0], [1.88, 1.0, 1.0]], (0.7, 0.4, -0.5), [0, 0, 0],
+                    [[c6]], [[c12]], [5.0, 5.0, 5.0], coulomb=coulomb, rc=1.0, beta=beta, eps_rf=1.0)
+
+
+def _pair_energies(s):
+    """Energies of each pair alone (two-atom sub-systems evaluated by brute force)."""
+    out = []
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        sub = dataclasses.replace(s, x=s.x[[i, j]], q=s.q[[i, j]], types=s.types[[i, j]],
+                                  excl_off=np.zeros(3, np.int32), excl_idx=np.zeros(0, np.int32))
+        o = oracle.brute(sub)
+        out.append((float(np.linalg.norm(s.x[i] - s.x[j])), o["E_lj"], o["E_c"]))
+    return out
+
+
+@pytest.mark.parametrize("coulomb,beta", [(synth.COULOMB_RF, 0.0), (synth.COULOMB_EWALD, 3.123413274340875)])
+def test_energy_moments_absolute_sums(coulomb, beta):
+    # sum |V| over pairs = sum of the absolute two-atom energies (the pair terms differ in sign,
+    # so this is not |E|)
+    s = _three_atoms(coulomb, beta)
+    pe = _pair_energies(s)
+    _, _, a_lj, a_c = oracle.energy_moments(s, with_abs=True)
+    assert a_lj == pytest.approx(sum(abs(v) for _, v, _ in pe), rel=1e-12)
+    assert a_c == pytest.approx(sum(abs(v) for _, _, v in pe), rel=1e-12)
+    assert a_lj > abs(sum(v for _, v, _ in pe)) * 1.01
+    assert a_c > abs(sum(v for _, _, v in pe)) * 1.01
+
+
+@pytest.mark.parametrize("coulomb,beta", [(synth.COULOMB_RF, 0.0), (synth.COULOMB_EWALD, 3.123413274340875)])
+def test_energy_hist_bins_the_pair_terms(coulomb, beta):
+    # each pair lands in bin floor(r / rc * nbins) with its own energy, square and charge product
+    s = _three_atoms(coulomb, beta)
+    nb = 40
+    h = oracle.energy_hist(s, nb)
+    want = np.zeros((nb, 6))
+    for (r, vlj, vc), (i, j) in zip(_pair_energies(s), ((0, 1), (0, 2), (1, 2))):
+        k = int(r / s.rc * nb)
+        want[k] += [1.0, s.q[i] * s.q[j], vlj, vlj * vlj, vc, vc * vc]
+    assert np.allclose(h, want, rtol=1e-12, atol=0.0)
+
+
+def test_energy_hist_adds_up_to_the_cell_list():
+    s = random_system(n=300, L=3.2, seed=17, n_types=3)
+    h = oracle.energy_hist(s, 64)
+    c = oracle.celllist(s)
+    assert int(h[:, 0].sum()) == c["npairs"]
+    assert h[:, 2].sum() == pytest.approx(c["E_lj"], rel=1e-12)
+    assert h[:, 4].sum() == pytest.approx(c["E_c"], rel=1e-12)
+    qq = sum(s.q[i] * s.q[j] for i, j, *_ in oracle.pairs_within(s, s.rc))
+    assert h[:, 1].sum() == pytest.approx(qq, rel=1e-12)
+
+
+def test_force_magnitude_sums():
+    # two atoms: each atom's sum of pair-force magnitudes is its force's magnitude; three
+    # atoms on a line: the sum of the two-atom force magnitudes, which exceeds the net force
+    s2 = two_atoms(0.37, q=(0.7, -0.4), rc=1.0)
+    o = oracle.brute(s2)
+    assert np.allclose(o["Fabs"], np.linalg.norm(o["F"], axis=1), rtol=1e-12)
+    s = _three_atoms(synth.COULOMB_EWALD, 3.123413274340875)
+    o = oracle.brute(s)
+    want = np.zeros(3)
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        sub = dataclasses.replace(s, x=s.x[[i, j]], q=s.q[[i, j]], types=s.types[[i, j]],
+                                  excl_off=np.zeros(3, np.int32), excl_idx=np.zeros(0, np.int32))
+        fij = np.linalg.norm(oracle.brute(sub)["F"][0])
+        want[i] += fij
+        want[j] += fij
+    assert np.allclose(o["Fabs"], want, rtol=1e-12)
+    assert np.all(o["Fabs"] >= np.linalg.norm(o["F"], axis=1))
+    # the cell list, its subset path and the image-pair evaluator agree with brute force
+    r = random_system(n=300, L=3.2, seed=19, n_types=3)
+    b = oracle.brute(r)
+    assert np.allclose(oracle.celllist(r)["Fabs"], b["Fabs"], rtol=1e-12)
+    sub = np.array([3, 50, 299])
+    assert np.allclose(oracle.celllist(r, subset=sub)["Fabs"], b["Fabs"][sub], rtol=1e-12)
+    assert np.allclose(oracle.listset(r, oracle.pairs_within(r, r.rc))["Fabs"], b["Fabs"], rtol=1e-12)
