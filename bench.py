@@ -5,12 +5,13 @@ rlist 1.1 nm) run as an MD-like loop: every step evaluates forces, energies
 and the virial from the inner list, re-prunes half of the outer list (rolling
 prune over 2 parts) and advances positions ballistically; every 100 steps the
 grid sort and the pair search rebuild the outer list.  `value` is steps (force
-evaluations) per second on the device; `e2e` the same through the public API
-with positions copied in from pinned host memory and forces/energies copied out
-every step.  Extra workloads (batched replicas, forward + adjoint, the 1.5M-atom
-box) are reported under "extra".
+evaluations) per second on the device, each step charged 1/100 of one timed list
+rebuild; `e2e` the same through the public API with positions copied in from
+pinned host memory and forces/energies copied out every step.  Extra workloads
+(batched replicas, forward + adjoint, the complete Ewald sum, the argon sweep,
+the 648-atom box's latency and the 1.5M-atom box) are reported under "extra".
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--full]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the reference arm) on the same
 workload and metric.  Under torchrun each rank evaluates its own independent
@@ -54,12 +55,13 @@ FLOPS_PER_PAIR = {
 
 
 # DRAM bytes (read + write) of one k_forces<Ewald, energy, virial> launch on the
-# 96k box from the ncu capture summarised in profiles/k_forces_spce_water_96k.md;
-# set to None whenever the force kernel changes until it is captured again.
-FORCE_KERNEL_DRAM_BYTES = 7620352
+# 96k box, from the committed ncu summary of that kernel (the capture named in
+# FORCE_KERNEL_CAPTURE); None whenever the force kernel has changed since it was taken.
+FORCE_KERNEL_DRAM_BYTES = None
 # From the same capture: FP32 (FMA) pipe and issue-slot utilisation of that launch,
 # in percent of active cycles (what bounds the kernel; None with the bytes above).
-FORCE_KERNEL_NCU_PCT = {"fma_pipe_active": 52.3, "issue_slots_busy": 73.4}
+FORCE_KERNEL_NCU_PCT = None
+FORCE_KERNEL_CAPTURE = None
 
 
 def rank_env():
@@ -93,8 +95,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 20):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
         self.thread = None
@@ -103,7 +106,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
             return
@@ -190,18 +193,74 @@ def run_ours(args, rank, world, local_rank):
     w = torch.empty(9, dtype=torch.float64, device=dev)
     flags = api.NB_ENERGY | api.NB_VIRIAL
     x = x0.clone()
+    # the headline runs in the sorted layout (nb_forces_sorted): between list builds the
+    # positions, velocities and forces stay in the context's cluster order, as an MD engine
+    # that integrates in its grid order keeps them; a rebuild goes through caller order
+    lay = {}
 
-    def step(t):
-        if t % NSTLIST == 0 and t > 0:
+    def export_sorted():
+        ns = ctx.n_slots()
+        if lay.get("ns") != ns:
+            lay.update(ns=ns, xq=torch.empty((ns, 4), dtype=torch.float32, device=dev),
+                       perm=torch.empty(ns, dtype=torch.int32, device=dev),
+                       f=torch.empty((ns, 4), dtype=torch.float32, device=dev))
+        ctx.nb_sorted_export(lay["xq"], lay["perm"])
+        valid = lay["perm"] >= 0
+        idx = lay["perm"].clamp(min=0).long()
+        # velocities as (vx, vy, vz, 0) per slot: the update is one contiguous add over the slots
+        # that leaves the charges (w) and the padding slots as they are
+        v4 = torch.zeros((ns, 4), dtype=torch.float32, device=dev)
+        v4[:, :3] = torch.where(valid[:, None], v.index_select(0, idx), torch.zeros((), device=dev))
+        lay["v4"], lay["valid"], lay["idx"] = v4, valid, idx
+
+    def to_caller():
+        x.index_copy_(0, lay["idx"][lay["valid"]], lay["xq"][lay["valid"], :3])
+
+    def rebuild():
+        if args.caller_order:
             ctx.build(x, box)
-        ctx.nb_forces(flags, x, f, e, w)
-        ctx.nb_prune_rolling(t % n_parts, n_parts)
-        x.add_(v, alpha=DT)
+        else:
+            to_caller()
+            ctx.build(x, box)
+            export_sorted()
+
+    def step(t, rebuild_ok=True, fl=flags):
+        if rebuild_ok and t % NSTLIST == 0 and t > 0:
+            rebuild()
+        if args.caller_order:
+            ctx.nb_forces(fl, x, f, e, w)
+            ctx.nb_prune_rolling(t % n_parts, n_parts)
+            x.add_(v, alpha=DT)
+        else:
+            ctx.nb_forces_sorted(fl, lay["xq"], lay["f"], e, w)
+            ctx.nb_prune_rolling(t % n_parts, n_parts)
+            lay["xq"].add_(lay["v4"], alpha=DT)
+
+    if not args.caller_order:
+        export_sorted()
 
     ctx.nb_trace_enable(True, kinds=[api.NB_TRACE_FORCES])  # creates the events before timing
     for t in range(args.warmup):
         step(t)
     torch.cuda.synchronize()
+    # one list rebuild (grid sort + pair search + first full prune, with the host read-back of
+    # the list sizes inside it) timed on its own, L2 flushed: every step of the headline is
+    # charged 1/NSTLIST of it, whatever the number of timed steps
+    build_ms = []
+    for _ in range(5):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        rebuild()
+        b.record()
+        torch.cuda.synchronize()
+        build_ms.append(a.elapsed_time(b))
+    # the timed steps start half-way through a list lifetime: the force kernel's time grows with
+    # the list's age as the atoms spread, and mid-life is its average
+    for t in range(NSTLIST // 2):
+        step(t, rebuild_ok=False)
+    torch.cuda.synchronize()
+    t_off = NSTLIST // 2
     for kind in range(4):
         ctx.nb_trace_read(kind)
     launches0 = ctx.nb_get_stats()["n_launches"]
@@ -211,19 +270,35 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank)
     clocks.start()
+    built = []
     for k in range(args.steps):
         flush()  # L2 flushed between timed steps (outside the events)
         ctx.nb_trace_enable(k % TRACE_EVERY == 0, kinds=[api.NB_TRACE_FORCES])
+        t = t_off + k
+        built.append(t % NSTLIST == 0)
         evs[k][0].record()
-        step(args.warmup + k)
+        step(t)
         evs[k][1].record()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    launches = ctx.nb_get_stats()["n_launches"] - launches0
+    # clock window: the timed region is a few ms, shorter than the sampling interval, so the
+    # same steps keep running (untimed, L2 flushed alike) for a further second of sampling
+    ctx.nb_trace_enable(False)
+    t_end = time.perf_counter() + 1.0
+    k = 0
+    while time.perf_counter() < t_end:
+        flush()
+        step(t_off + args.steps + k)
+        k += 1
+        if k % 50 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
     clk = clocks.stop()
+    t_off += args.steps + k
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
-    launches = ctx.nb_get_stats()["n_launches"] - launches0
     fk_ms, fk_n = ctx.nb_trace_read(api.NB_TRACE_FORCES)
     assert ctx.nb_get_error() == 0, "device error during the timed loop"
     # algorithmic work of one force launch: effective pairs at the current positions
@@ -233,11 +308,14 @@ def run_ours(args, rank, world, local_rank):
     ctx.nb_trace_enable(True, kinds=[api.NB_TRACE_PRUNE, api.NB_TRACE_GATHER])
     for k in range(50):
         flush()
-        step(args.warmup + args.steps + k)
+        step(t_off + k)
     pr_ms, pr_n = ctx.nb_trace_read(api.NB_TRACE_PRUNE)
     ga_ms, ga_n = ctx.nb_trace_read(api.NB_TRACE_GATHER)
     ctx.nb_trace_enable(False)
+    plain_steps = [m for m, b in zip(step_ms, built) if not b] or step_ms
     res = dict(total_ms=total_ms, step_ms=step_ms, launches=launches, fk_ms=fk_ms, fk_n=fk_n, pr_ms=pr_ms,
+               build_ms=float(np.median(build_ms)), step_mean_ms=float(np.mean(plain_steps)),
+               step_median_ms=float(np.median(plain_steps)), n_built_in_loop=int(sum(built)),
                pr_n=pr_n, ga_ms=ga_ms, ga_n=ga_n, n_eff=n_eff, n_raw=n_raw, clocks=clk, n_atoms=s.n,
                tuned={"split": int(tuned["split"]), "n_parts": n_parts})
     # end to end through the public API: pinned host positions in, forces + energies out
@@ -268,24 +346,34 @@ def run_ours(args, rank, world, local_rank):
         eh.copy_(eo, non_blocking=True)
         wh.copy_(wo.view(-1), non_blocking=True)
         torch.cuda.synchronize()
-        if k >= args.warmup:
+        if k >= args.warmup and t % NSTLIST:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
         xh.add_(vh, alpha=DT)
     res["e2e_ms"] = float(np.mean(e2e_ms))
+    # a rebuild through the same API (positions copied in, grid sort, search, first prune),
+    # host wall clock; charged 1/NSTLIST per step like the device-timed headline
+    eb = []
+    for _ in range(3):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd.copy_(xh, non_blocking=True)
+        ctx.build(xd, box)
+        torch.cuda.synchronize()
+        eb.append((time.perf_counter() - t0) * 1e3)
+    res["e2e_build_ms"] = float(np.median(eb))
     # context: energies and virial only every 100th step and forces alone otherwise, the cadence
     # MD engines compute them at; the same loop from the same start, device time, L2 flushed
     x.copy_(x0)
     ctx.build(x, box)
+    if not args.caller_order:
+        export_sorted()
     ev100 = []
     for k in range(args.warmup + args.steps):
         flush()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        if k % NSTLIST == 0 and k > 0:
-            ctx.build(x, box)
-        ctx.nb_forces(flags if k % 100 == 0 else 0, x, f, e, w)
-        ctx.nb_prune_rolling(k % n_parts, n_parts)
-        x.add_(v, alpha=DT)
+        step(k, fl=flags if k % 100 == 0 else 0)
         b.record()
         if k >= args.warmup:
             ev100.append((a, b))
@@ -293,6 +381,7 @@ def run_ours(args, rank, world, local_rank):
     res["md_e100_ms"] = float(np.mean([a.elapsed_time(b) for a, b in ev100]))
     res["h2d"] = s.n * 3 * 4
     res["d2h"] = s.n * 3 * 4 + 16 + 72
+    res["layout"] = "caller order" if args.caller_order else "sorted (nb_forces_sorted)"
     return res
 
 
@@ -502,18 +591,41 @@ def extra_workloads(args):
                       "work_efficiency": n_eff / max(n_raw, 1)})
         del ca
     out["argon_157k_sweep"] = sweep
-    if args.full:
-        s3 = synth.polymer_water_box()
-        c3 = api.NbContext.from_system(s3)
-        x3 = torch.tensor(s3.x, device=dev)
-        c3.build(x3, s3.box)
-        f3 = torch.empty_like(x3)
-        e3 = torch.empty(2, dtype=torch.float64, device=dev)
-        w3 = torch.empty(9, dtype=torch.float64, device=dev)
-        t3 = time_fn(lambda: c3.nb_forces(flags, x3, f3, e3, w3), reps_=10)
-        n_eff, n_raw = c3.nb_count_pairs()
-        out["polymer_water_1.5M"] = {"n_atoms": s3.n, "force_ms": t3, "evals_per_s": 1e3 / t3,
-                                     "effective_pairs": int(n_eff), "evaluated_pairs": int(n_raw)}
+    # the 648-atom reaction-field box: latency of one evaluation (forces + energies + virial;
+    # gather, force kernel, unsort) issued eagerly and replayed from a CUDA graph
+    s1 = synth.water_648()
+    c1 = api.NbContext.from_system(s1)
+    x1 = torch.tensor(s1.x, device=dev)
+    c1.build(x1, s1.box)
+    f1 = torch.empty_like(x1)
+    e1 = torch.empty(2, dtype=torch.float64, device=dev)
+    w1 = torch.empty(9, dtype=torch.float64, device=dev)
+
+    def ev648():
+        c1.nb_forces(flags, x1, f1, e1, w1)
+    t1_eager = time_fn(ev648, reps_=200, warm=20)
+    g1 = graphed(ev648)
+    t1_graph = time_fn(g1.replay, reps_=200, warm=20)
+    out["water_648_rf_latency"] = {"n_atoms": s1.n, "us_per_eval_eager": 1e3 * t1_eager,
+                                   "us_per_eval_graph": 1e3 * t1_graph,
+                                   "note": "median of 200 evaluations, CUDA events, L2 flushed between them"}
+    del g1, c1
+    # the 1.5M-atom heterogeneous box (85% water, 15% polymer, 22 LJ types, rc 1.2 nm):
+    # force + energy + virial evaluations from a fresh list
+    s3 = synth.polymer_water_box()
+    c3 = api.NbContext.from_system(s3)
+    x3 = torch.tensor(s3.x, device=dev)
+    c3.build(x3, s3.box)
+    f3 = torch.empty_like(x3)
+    e3 = torch.empty(2, dtype=torch.float64, device=dev)
+    w3 = torch.empty(9, dtype=torch.float64, device=dev)
+    t3 = time_fn(lambda: c3.nb_forces(flags, x3, f3, e3, w3), reps_=8, warm=2)
+    n_eff, n_raw = c3.nb_count_pairs()
+    out["polymer_water_1.5M"] = {"n_atoms": s3.n, "force_ms": t3, "evals_per_s": 1e3 / t3,
+                                 "effective_pairs": int(n_eff), "evaluated_pairs": int(n_raw),
+                                 "effective_Gpairs_per_s": n_eff / (t3 * 1e-3) / 1e9,
+                                 "note": "median of 8 calls (gather + force kernel + unsort), L2 flushed"}
+    del c3
     return out
 
 
@@ -555,13 +667,16 @@ def main_ours(args):
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     torch.cuda.set_device(local_rank)
     res = run_ours(args, rank, world, local_rank)
-    ms, res["e2e_ms"] = max_over_ranks([res["total_ms"], res["e2e_ms"]], "cuda")
+    # the headline step: the mean timed step (forces + energies + virial, half-list rolling
+    # prune, position update) plus 1/NSTLIST of one timed list rebuild
+    amort = res["step_mean_ms"] + res["build_ms"] / NSTLIST
+    e2e_amort = res["e2e_ms"] + res["e2e_build_ms"] / NSTLIST
+    ms_per_step, res["e2e_ms"], res["total_ms"] = max_over_ranks([amort, e2e_amort, res["total_ms"]], "cuda")
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = world * 1e3 / ms_per_step
     clk = res["clocks"]
     peak, sms = fp32_peak_tflops(clk.get("sm_mhz"))
     fk_avg_ms = res["fk_ms"] / max(res["fk_n"], 1)
@@ -573,6 +688,16 @@ def main_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "spce_water_96k_ewald_rc1.0_rlist1.1 MD-like step: forces+energies+virial, "
                                "rolling prune of 1/2 of the list per step, grid sort + pair search every 100 steps",
+                   "e2e_step": "caller atom order through NbContext.forces (gather and scatter included), pinned "
+                               "host positions in and forces, energies, virial out every step",
+                   "step": "mean of the timed steps without a rebuild (forces+energies+virial, half-list rolling "
+                           "prune, position update) + 1/100 of one list rebuild (grid sort + pair search + first "
+                           "full prune) timed on its own with CUDA events; steps start half-way through a list "
+                           "lifetime",
+                   "layout": res["layout"],
+                   "step_mean_ms": res["step_mean_ms"], "step_median_ms": res["step_median_ms"],
+                   "rebuild_ms": res["build_ms"], "rebuilds_inside_timed_steps": res["n_built_in_loop"],
+                   "timed_region_ms": res["total_ms"],
                    "n_atoms": res["n_atoms"], "rc": 1.0, "rlist": 1.1, "r_in": 1.0, "nstlist": NSTLIST,
                    "prune_parts": res["tuned"]["n_parts"], "split": res["tuned"]["split"],
                    "l2": "flushed between timed steps (256 MiB write + 256 MiB read of another buffer, outside the events)",
@@ -582,16 +707,18 @@ def main_ours(args):
         "gpu_launches": int(res["launches"]),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": FORCE_KERNEL_DRAM_BYTES,
-                     "ncu_pct": FORCE_KERNEL_NCU_PCT,
+                     "traffic_source": FORCE_KERNEL_CAPTURE, "ncu_pct": FORCE_KERNEL_NCU_PCT,
                      "kernel": "k_forces<Ewald, energy, virial>", "avg_launch_ms": fk_avg_ms,
                      "timed_launches": int(res["fk_n"]),
                      "launch_timing": f"CUDA events around every {TRACE_EVERY}th force launch of the timed loop",
                      "effective_pairs_per_launch": int(res["n_eff"]), "evaluated_pairs_per_launch": int(res["n_raw"]),
                      "flops_per_effective_pair": FLOPS_PER_PAIR[("ewald", "FEV")],
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x median SM clock under load"},
-        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons")},
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons"),
+                   "samples": clk.get("samples"),
+                   "window": "nvidia-smi every 20 ms over the timed steps and one further second of the same steps"},
         "kernels_ms_per_step": {"forces": fk_avg_ms, "prune": res["pr_ms"] / max(res["pr_n"], 1),
-                                "gather": res["ga_ms"] / max(res["ga_n"], 1)},
+                                ("gather" if args.caller_order else "prep_sorted"): res["ga_ms"] / max(res["ga_n"], 1)},
         "pairs_per_s_effective": res["n_eff"] / (fk_avg_ms * 1e-3),
     }
     if not args.no_extra:
@@ -746,8 +873,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--full", action="store_true", help="also time the 1.5M-atom polymer/water box")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
+    ap.add_argument("--caller-order", action="store_true",
+                    help="run the headline loop in caller atom order (nb_forces: gather and scatter every step) "
+                         "instead of the sorted layout")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true",
                     help="profiling target: warmup + steps force evaluations (energy+virial) of the 96k box only")

@@ -166,6 +166,32 @@ nb_status nb_prune_rolling(nb_ctx *ctx, float r_in, int part, int n_parts, void 
 nb_status nb_forces(nb_ctx *ctx, unsigned flags, const float *x_dev, float *f_dev, double *e_dev,
                     double *vir_dev, void *stream);
 
+/* Sorted-layout mode (not in the paper): between two list builds a caller may
+ * keep positions and forces in the context's cluster order -- the order the
+ * grid sort gives, 64 slots per super-cluster with padding slots -- and so skip
+ * the per-step gather of caller-order positions into that order and the scatter
+ * of the forces back.  n_slots is nb_stats.n_slots after nb_grid_sort.
+ *
+ * nb_sorted_export copies to caller buffers the sorted positions and charges of
+ * the last grid sort, xq_dev [n_slots*4] (x, y, z, q per slot; positions are the
+ * periodic images the sort chose; padding slots hold far-away positions and
+ * q = 0), and the permutation perm_dev [n_slots] (caller index of the atom in
+ * each slot, -1 for padding; either pointer may be NULL).  Asynchronous.
+ * NB_ERR_NOT_READY before the first grid sort. */
+nb_status nb_sorted_export(nb_ctx *ctx, float *xq_dev, int32_t *perm_dev, void *stream);
+
+/* Forces at sorted positions xq_dev [n_slots*4] (as exported, x, y, z then moved
+ * by the caller; q and the padding slots left as exported).  Writes f_dev
+ * [n_slots*4] (force x, y, z per slot, w = 0; padding slots 0; overwritten) and,
+ * with NB_ENERGY / NB_VIRIAL, e_dev[2] / vir_dev[9] as nb_forces.  Positions are
+ * used as given: no wrapping, no image offsets.  The context keeps xq_dev as the
+ * positions of its last force call, which nb_prune_rolling and nb_count_pairs
+ * read: it must stay valid and unchanged until they have run (a later nb_forces
+ * or nb_grid_sort makes the context use its own copy again).  Asynchronous;
+ * never allocates; calls on one context must not overlap on the GPU. */
+nb_status nb_forces_sorted(nb_ctx *ctx, unsigned flags, const float *xq_dev, float *f_dev, double *e_dev,
+                           double *vir_dev, void *stream);
+
 /* Adjoint of nb_forces (not in the paper): for L = <gF, F> + gE*(E_LJ + E_C),
  * recomputes every pair of the inner list at x_dev and writes gx_dev [N*3],
  * gq_dev [N] (FP32, overwritten) and gc6_dev / gc12_dev [T*T] (FP64,
@@ -301,27 +327,34 @@ nb_status nb_ewald_corrections(nb_ctx *ctx, unsigned flags, const float *x_dev, 
 /* ------------------------------------------------------------------------
  * Allocation-free evaluation of one small system.  The paper has no
  * counterpart: it exists for callers that cannot allocate device memory, such
- * as code running while a stream is captured into a CUDA graph (cudaMalloc is
- * not permitted there), code whose device memory belongs to another allocator,
- * and latency-critical code that cannot risk the device synchronisation
- * cudaMalloc/cudaFree may cause.  It needs no context and no pair list: all
- * pairs of the system are evaluated with the same pair interactions as
- * nb_forces (inputs: params (rlist and r_in are ignored), x_dev [N*3], q_dev [N],
- * type_dev [N], optional device exclusion CSR excl_off_dev [N+1] /
- * excl_idx_dev (both NULL for none, at most 16 partners per atom), box_host [3];
- * outputs as nb_forces: f_dev [N*3] overwritten, e_dev [2] with NB_ENERGY,
- * vir_dev [9] with NB_VIRIAL).
+ * as code whose device memory belongs to another allocator (a framework's
+ * caching allocator, or a pool reserved at start-up), code that is not allowed
+ * to allocate once it is running, and latency-critical code that cannot risk
+ * the device synchronisation cudaMalloc/cudaFree may cause.  It needs no
+ * context and no pair list: all pairs of the system are evaluated with the same
+ * pair interactions as nb_forces (inputs: params (rlist and r_in are ignored),
+ * x_dev [N*3], q_dev [N], type_dev [N] with every type in [0, n_types),
+ * optional device exclusion CSR excl_off_dev [N+1] / excl_idx_dev (both NULL
+ * for none, at most 16 partners per atom), box_host [3]; outputs as nb_forces:
+ * f_dev [N*3] overwritten, e_dev [2] with NB_ENERGY, vir_dev [9] with
+ * NB_VIRIAL).
  *
  * Its scratch is a file-scope static device array of about 410 KB that every
  * GPU loading the library holds until the process exits.  Limits: N <=
  * NB_NOALLOC_MAX_ATOMS and T <= NB_NOALLOC_MAX_TYPES; larger sizes return
- * NB_ERR_CAPACITY before any work is enqueued.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
- * the one array (each call overwrites what it reads, nothing has to start at
- * zero), so calls whose work overlaps on the GPU -- e.g. on two streams
- * without ordering -- race and give wrong results; order them on one stream.
- * Never allocates.  Intended for small systems: the work is O(N^2). */
+ * NB_ERR_CAPACITY before any work is enqueued.  Types and exclusion rows live
+ * in device memory, so they are checked on the device: if any type lies
+ * outside [0, T) or any exclusion row is malformed or longer than 16 entries,
+ * the call still returns NB_OK but writes NaN to every force component and to
+ * every requested energy and virial entry.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current
+ * and keeps it for the life of the process; make that first call before any
+ * stream capture, and do not use this entry point on a device after
+ * cudaDeviceReset (the address it kept is then stale).  All calls share the one
+ * array (each call clears its status word and overwrites what it reads), so
+ * calls whose work overlaps on the GPU -- e.g. on two streams without ordering
+ * -- race and give wrong results; order them on one stream.  Never allocates.
+ * Intended for small systems: the work is O(N^2). */
 #define NB_NOALLOC_MAX_ATOMS 16384
 #define NB_NOALLOC_MAX_TYPES 8
 nb_status nb_forces_small_noalloc(const nb_params *params, const float *x_dev, const float *q_dev,

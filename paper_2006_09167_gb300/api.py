@@ -127,6 +127,33 @@ class NbContext:
         check(self._lib.nb_forces(self.handle, ctypes.c_uint(flags), _dev(x, torch.float32, 3 * self.n, "x"),
                                   _dev(f, torch.float32, 3 * self.n, "f"), ep, vp, _stream(stream)), "nb_forces")
 
+    def n_slots(self) -> int:
+        """Slots of the sorted layout (64 per super-cluster, padding included)."""
+        return int(self.nb_get_stats()["n_slots"])
+
+    def nb_sorted_export(self, xq: Optional[torch.Tensor] = None, perm: Optional[torch.Tensor] = None, stream=None):
+        """Sorted positions and charges [n_slots, 4] and the slot -> atom permutation [n_slots]
+        (-1 for padding) of the last grid sort, into the given tensors or new ones."""
+        ns = self.n_slots()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if xq is None:
+            xq = torch.empty((ns, 4), dtype=torch.float32, device=dev)
+        if perm is None:
+            perm = torch.empty(ns, dtype=torch.int32, device=dev)
+        check(self._lib.nb_sorted_export(self.handle, _dev(xq, torch.float32, 4 * ns, "xq"),
+                                         _dev(perm, torch.int32, ns, "perm"), _stream(stream)), "nb_sorted_export")
+        return xq, perm
+
+    def nb_forces_sorted(self, flags: int, xq: torch.Tensor, f: torch.Tensor, e: Optional[torch.Tensor] = None,
+                         vir: Optional[torch.Tensor] = None, stream=None):
+        """Forces [n_slots, 4] at the sorted positions xq [n_slots, 4] (see nb_forces_sorted)."""
+        ns = self.n_slots()
+        ep = _dev(e, torch.float64, 2, "e") if (flags & NB_ENERGY) else None
+        vp = _dev(vir, torch.float64, 9, "vir") if (flags & NB_VIRIAL) else None
+        check(self._lib.nb_forces_sorted(self.handle, ctypes.c_uint(flags), _dev(xq, torch.float32, 4 * ns, "xq"),
+                                         _dev(f, torch.float32, 4 * ns, "f"), ep, vp, _stream(stream)),
+              "nb_forces_sorted")
+
     def nb_forces_vjp(self, x, gF, gE: float, gx, gq, gc6, gc12, stream=None):
         tt = self.T * self.T
         check(self._lib.nb_forces_vjp(self.handle, _dev(x, torch.float32, 3 * self.n, "x"),

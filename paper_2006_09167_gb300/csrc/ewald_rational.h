@@ -8,7 +8,7 @@
  */
 #pragma once
 #define NB_EW_ZMAX 4.0f
-/* H: degrees (6,5); fp64 max rel err 6.29e-08; fp32 Horner max rel err 3.47e-07, mean -1.41e-08 */
+/* H: degrees (6,5); fp64: max rel err 6.29e-08; fp32 Horner max rel err 3.47e-07, mean -1.41e-08 */
 #define NB_EW_HP0 0.7522528171539307f
 #define NB_EW_HP1 -0.5743048191070557f
 #define NB_EW_HP2 4.628017902374268f
@@ -21,16 +21,20 @@
 #define NB_EW_HQ3 88.59178924560547f
 #define NB_EW_HQ4 137.36947631835938f
 #define NB_EW_HQ5 136.4874267578125f
-/* X: degrees (4,4); fp64 max rel err 1.1e-08; fp32 Horner max rel err 3.32e-07, mean 7.62e-09 */
+/* X: degrees (6,6); FP32 coefficients, exact evaluation: max rel err 2.88e-09; fp32 Horner max rel err 3.6e-07, mean 5.81e-09 */
 #define NB_EW_XP0 1.0f
-#define NB_EW_XP1 3.465115547180176f
-#define NB_EW_XP2 5.828225612640381f
-#define NB_EW_XP3 3.9410693645477295f
-#define NB_EW_XP4 0.002993972273543477f
-#define NB_EW_XQ1 7.978628158569336f
-#define NB_EW_XQ2 25.840158462524414f
-#define NB_EW_XQ3 41.050724029541016f
-#define NB_EW_XQ4 28.053558349609375f
+#define NB_EW_XP1 5.064917087554932f
+#define NB_EW_XP2 12.871368408203125f
+#define NB_EW_XP3 18.6243839263916f
+#define NB_EW_XP4 15.265811920166016f
+#define NB_EW_XP5 5.703533172607422f
+#define NB_EW_XP6 0.0005424104747362435f
+#define NB_EW_XQ1 9.578433990478516f
+#define NB_EW_XQ2 40.103782653808594f
+#define NB_EW_XQ3 94.52271270751953f
+#define NB_EW_XQ4 133.38247680664062f
+#define NB_EW_XQ5 108.19001007080078f
+#define NB_EW_XQ6 40.45461654663086f
 /* exp: degree 7; fp64 max rel err 4.67e-11; fp32 exp(-x) on [0,16] max rel err 7.23e-08, mean -1.8e-10 */
 #define NB_EXP_LOG2E 1.4426950216293335f
 #define NB_EXP_LN2_HI 0.693145751953125f

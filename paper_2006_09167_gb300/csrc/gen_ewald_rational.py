@@ -17,12 +17,20 @@ Forming erfc(z)/r as 1/r - beta erf(z)/z instead would subtract two O(1/r)
 numbers and lose most FP32 digits near the cut-off.
 
 Accuracy requirement.  The Coulomb energy of water is a sum of terms that cancel
-by a factor of about 3000 (sum |V| / |sum V|), so a pointwise relative error
-that varies smoothly with r -- such as the equioscillating error of a fit -- is
-amplified by that factor instead of averaging out.  The fits are therefore
-taken to a fit error well below the FP32 rounding level (exp: ~5e-11, degree 7;
-a degree-6 polynomial with 2e-9 moved the energy of a 96,000-atom water box by
-4e-6 relative, the degree-7 one leaves it at the FP32 floor).
+by a factor of about 3000 (sum |V| / |sum V|; 44,000 for the 1.5M-atom polymer
+box), so a pointwise relative error that varies smoothly with r -- such as the
+equioscillating error of a fit -- is amplified by that factor instead of
+averaging out.  The fits are therefore taken to a fit error well below the FP32
+rounding level (exp: ~5e-11, degree 7; a degree-6 polynomial with 2e-9 moved
+the energy of a 96,000-atom water box by 4e-6 relative, the degree-7 one leaves
+it at the FP32 floor).  For X the limit is not the fit but the FP32 rounding
+of its coefficients: rounding the coefficients of a minimax (4,4) rational
+(fit error 1.1e-8) to FP32 leaves a smooth error of 3.5e-8, which the
+polymer box's energy amplified to 1.4e-5.  X is therefore a (6,6) rational
+whose coefficients are chosen among FP32 values: starting from the FP64 fit,
+the coefficient whose rounding moves the function most is rounded and fixed,
+the remaining ones are fitted again, and so on (largest smooth error 2.9e-9;
+the polymer box's energy error predicted from it 2e-7).
 
 H is fitted as P(s)/Q(s) in s = z^2/ZMAX^2 and X as P(t)/Q(t) in t = z/ZMAX
 (ZMAX = 4, i.e. beta*rc <= 4), each with Q(0) = 1, and exp(w) as
@@ -39,7 +47,7 @@ import numpy as np
 
 ZMAX = 4.0
 DEG_H = (6, 5)
-DEG_X = (4, 4)
+DEG_X = (6, 6)
 DEG_EXP = 7
 mpmath.mp.dps = 40
 
@@ -78,6 +86,61 @@ def fit(fun, m, n, iters=40, npts=3000, squared=True):
         w = w * np.abs(r) ** 0.5 + 1e-30
         w /= w.max()
     return best
+
+
+def fit_fp32_coefficients(fun, m, n, squared=False, iters=60, npts=3000):
+    """Minimax relative fit P/Q (Q(0) = 1, P(0) = fun(0) = 1) with FP32 coefficients.
+
+    Rounding all FP64 coefficients to FP32 at once leaves an error far above the
+    fit's (each coefficient of a rational moves the function by up to ~1e-8).
+    Instead, one coefficient at a time -- the one whose rounding moves the
+    function most, at the current fit -- is rounded to FP32 and fixed, and the
+    free ones are fitted again (the same re-weighted least squares as fit()),
+    so the later coefficients absorb the rounding of the earlier ones."""
+    k = np.arange(npts)
+    s = 0.5 * (1 - np.cos(np.pi * (k + 0.5) / npts))
+    f = np.array([float(fun(ZMAX * (np.sqrt(v) if squared else v))) for v in s])
+    ncoef = m + 1 + n
+    A = np.concatenate([np.vander(s, m + 1, increasing=True),
+                        -f[:, None] * np.vander(s, n + 1, increasing=True)[:, 1:]], 1)
+
+    def solve(frozen):
+        free = [c for c in range(ncoef) if c not in frozen]
+        rhs0 = f - sum(A[:, c] * v for c, v in frozen.items())
+        w = np.ones_like(s)
+        q = np.ones_like(s)
+        best = None
+        for _ in range(iters if free else 1):
+            coef = np.zeros(ncoef)
+            if free:
+                wt = w / (np.abs(q) * np.abs(f))
+                sol, *_ = np.linalg.lstsq(A[:, free] * wt[:, None], rhs0 * wt, rcond=None)
+                coef[free] = sol
+            for c, v in frozen.items():
+                coef[c] = v
+            q = np.polyval(np.concatenate([[1.0], coef[m + 1:]])[::-1], s)
+            r = (np.polyval(coef[:m + 1][::-1], s) / q - f) / f
+            e = np.abs(r).max()
+            if best is None or e < best[0]:
+                best = (e, coef.copy())
+            w = w * np.abs(r) ** 0.5 + 1e-30
+            w /= w.max()
+        return best
+
+    frozen = {0: 1.0}
+    e, coef = solve(frozen)
+    while len(frozen) < ncoef:
+        P = np.polyval(coef[:m + 1][::-1], s)
+        Q = np.polyval(np.concatenate([[1.0], coef[m + 1:]])[::-1], s)
+        moved = {}
+        for c in range(ncoef):
+            if c not in frozen:
+                basis = s ** c / P if c <= m else s ** (c - m) / Q
+                moved[c] = np.abs((float(np.float32(coef[c])) - coef[c]) * basis).max()
+        c = max(moved, key=moved.get)
+        frozen[c] = float(np.float32(coef[c]))
+        e, coef = solve(frozen)
+    return e, coef[:m + 1], np.concatenate([[1.0], coef[m + 1:]])
 
 
 def fit_exp(deg, iters=60, npts=4000):
@@ -158,9 +221,14 @@ def main():
     out.append("#pragma once")
     out.append(f"#define NB_EW_ZMAX {ZMAX:.1f}f")
     for name, fun, (m, n), sq in (("H", h_ref, DEG_H, True), ("X", x_ref, DEG_X, False)):
-        e, p, qc = fit(fun, m, n, squared=sq)
+        if name == "X":
+            e, p, qc = fit_fp32_coefficients(fun, m, n, squared=sq)
+            kind = "FP32 coefficients, exact evaluation"
+        else:
+            e, p, qc = fit(fun, m, n, squared=sq)
+            kind = "fp64"
         e32, b32 = f32_horner_error(fun, p, qc, squared=sq)
-        out.append(f"/* {name}: degrees ({m},{n}); fp64 max rel err {e:.3g}; "
+        out.append(f"/* {name}: degrees ({m},{n}); {kind}: max rel err {e:.3g}; "
                    f"fp32 Horner max rel err {e32:.3g}, mean {b32:.3g} */")
         for i, c in enumerate(p):
             out.append(f"#define NB_EW_{name}P{i} {float(np.float32(c))!r}f")

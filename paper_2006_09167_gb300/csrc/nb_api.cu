@@ -81,7 +81,7 @@ __global__ void k_set_q(int n, const float *__restrict__ q, float *__restrict__ 
 
 nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     nbk::SysView v;
-    v.xq = c->xq;
+    v.xq = nb_cur_xq(c);
     v.type = c->type_s;
     v.items = c->items;
     v.inner_len = c->inner_len;
@@ -120,6 +120,8 @@ nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     v.kept = nullptr;
     v.rin2 = 0.f;
     v.ew_beta2 = (float)(c->beta * c->beta);
+    v.ew_beta_lo = (float)(c->beta - (double)v.ew_beta);
+    v.ew_beta2_lo = (float)(c->beta * c->beta - (double)v.ew_beta2);
     v.ew_2bsp = (float)(2.0 * c->beta / sqrt(M_PI));
     return v;
 }
@@ -388,6 +390,7 @@ nb_status nb_grid_sort(nb_ctx *c, const float *x_dev, const double *box, void *s
     }
     if ((s = nb_launch_grid_sort_phase2(c, hc[1], st)) != NB_OK) return s;
     c->have_grid = true;
+    c->xq_cur = nullptr;
     return NB_OK;
 }
 
@@ -490,6 +493,31 @@ nb_status nb_forces(nb_ctx *c, unsigned flags, const float *x_dev, float *f_dev,
         return NB_OK;
     }
     return nb_launch_forces(c, flags, f_dev, e_dev, vir_dev, st);
+}
+
+nb_status nb_sorted_export(nb_ctx *c, float *xq_dev, int32_t *perm_dev, void *stream) {
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (!c->have_grid) return NB_ERR_NOT_READY;
+    const size_t ns = (size_t)c->S_host * NB_SCA;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (xq_dev) NB_CUDA_TRY(cudaMemcpyAsync(xq_dev, c->xq, sizeof(float4) * ns, cudaMemcpyDeviceToDevice, st));
+    if (perm_dev) NB_CUDA_TRY(cudaMemcpyAsync(perm_dev, c->perm, sizeof(int) * ns, cudaMemcpyDeviceToDevice, st));
+    return NB_OK;
+}
+
+nb_status nb_forces_sorted(nb_ctx *c, unsigned flags, const float *xq_dev, float *f_dev, double *e_dev,
+                           double *vir_dev, void *stream) {
+    if (!c || !xq_dev || !f_dev) return NB_ERR_INVALID_ARG;
+    if (flags & ~(unsigned)(NB_ENERGY | NB_VIRIAL)) return NB_ERR_INVALID_ARG;
+    if ((flags & NB_ENERGY) && !e_dev) return NB_ERR_INVALID_ARG;
+    if ((flags & NB_VIRIAL) && !vir_dev) return NB_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(xq_dev) | reinterpret_cast<uintptr_t>(f_dev)) & 15) return NB_ERR_INVALID_ARG;
+    if (!c->have_list) return NB_ERR_NOT_READY;
+    cudaStream_t st = (cudaStream_t)stream;
+    // a pending first-use prune runs first, at the positions of the last sort
+    if (nb_status s = nb_ensure_inner(c, st); s != NB_OK) return s;
+    return nb_launch_forces_sorted(c, flags, reinterpret_cast<const float4 *>(xq_dev), reinterpret_cast<float4 *>(f_dev),
+                                   e_dev, vir_dev, st);
 }
 
 nb_status nb_forces_vjp(nb_ctx *c, const float *x_dev, const float *gF_dev, double gE, float *gx_dev,

@@ -188,6 +188,7 @@ nb_status nb_batch_create(nb_ctx *const *ctxs, int n, nb_batch **out) {
     cudaError_t err = cudaSuccess;
     for (int r = 0; r < n && err == cudaSuccess; r++) {
         nb_ctx *c = ctxs[r];
+        c->xq_cur = nullptr;  // the batched gather writes the context's own positions
         views[r] = nb_make_view(c, c->fs, nullptr, nullptr);
         BatchRep &p = reps[r];
         p.perm = c->perm;

@@ -7,9 +7,9 @@
 // branch, so no divergence).  Lane (ti, tj) = (lane & 7, lane >> 3) computes
 // the pairs (i-atom ti, j-atom tj) and (ti, tj + 4) of every 8x8 cluster pair,
 // so each j-atom is loaded once per entry and reused for all 8 i-clusters.
-// i-forces stay in registers for the whole item; j-forces are reduced over the
-// 8 ti lanes by shuffles at the end of each j iteration and added once per
-// j-atom.  Each pair is computed once (Newton's third law).  Exclusions and the
+// i-forces accumulate in per-warp shared memory for the whole item; j-forces are
+// reduced over the 8 ti lanes by shuffles at the end of each j iteration and
+// added once per j-atom.  Each pair is computed once (Newton's third law).  Exclusions and the
 // self-pair triangle come from the entry's bit masks and are applied together
 // with the cut-off test.  Pair arithmetic is FP32; energies and the virial are
 // accumulated per lane in FP32 over one item and reduced in FP64.
@@ -17,9 +17,10 @@
 // Separate kernels per Coulomb type and energy/virial output (template
 // instantiations) avoid runtime conditionals in the inner loop (Sec. V.A).
 //
-// Ewald real space: phi_C = f qi qj (1/r^3 - beta^3 H(z)), V_C = f qi qj (1/r -
-// beta E(z) - erfc(beta rc)/rc) with z = beta r, evaluated with the FMA-only
-// rational approximations of ewald_rational.h plus one fast reciprocal.
+// Ewald real space: force-only kernels use phi_C = f qi qj (1/r^3 - beta^3 H(z)),
+// z = beta r, with the FMA-only rational H of ewald_rational.h; the energy
+// kernels form exp(-z^2) once and take erfc(z) = exp(-z^2) X(z) and the force
+// from it (nb_pair.cuh), V_C = f qi qj (erfc(z)/r - erfc(beta rc)/rc).
 #include <algorithm>
 
 #include "nb_pair.cuh"
@@ -126,6 +127,23 @@ __global__ void k_gather(int nslots, const int *__restrict__ perm, const float *
     xq[s] = make_float4(p[0], p[1], p[2], q_s[s]);
 }
 
+// Sorted-layout mode: zero the caller's sorted force array, the energy / virial
+// outputs and the work-item counter, and prefetch the lists into L2 (as the
+// gather does when it also brings in the positions).
+__global__ void k_prep_sorted(int nslots, float4 *__restrict__ f, double *e, double *vir, int *queue, L2Prefetch pf) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < 5; r++)
+        if (s < pf.lines[r]) asm volatile("prefetch.global.L2 [%0];" ::"l"(pf.p[r] + (size_t)s * 128));
+    if (s == 0) {
+        *queue = 0;
+        if (e) e[0] = e[1] = 0.0;
+        if (vir)
+            for (int k = 0; k < 9; k++) vir[k] = 0.0;
+    }
+    if (s < nslots) f[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Forces back to caller order; each block also folds a share of the per-block
 // energy/virial partial sums into the FP64 outputs (E_C gets the Coulomb
 // constant here, the virial its factor -1/2).
@@ -180,22 +198,31 @@ void launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
 
 }  // namespace
 
-nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cudaStream_t st) {
-    const int ns = c->S_host * NB_SCA;
-    NbTraceScope tr(c, NB_TRACE_GATHER, st);
-    c->n_launches++;
+// Lines of the lists the force kernel reads, for an L2 prefetch before it runs.
+static L2Prefetch list_prefetch(const nb_ctx *c, long long *most) {
     L2Prefetch pf;
+    const int ns = c->S_host * NB_SCA;
     const bool lists = c->have_list;
     const void *base[5] = {c->cj_inner, c->items, c->inner_len, c->type_s, c->mask_lanes};
     const long long bytes[5] = {lists ? (long long)c->n_j * 8 : 0, lists ? (long long)c->n_items * 16 : 0,
                                 lists ? (long long)c->n_items * 4 : 0, (long long)ns * 4,
                                 lists ? (long long)c->n_masks * 64 : 0};
-    long long most = 0;
+    *most = 0;
     for (int r = 0; r < 5; r++) {
         pf.p[r] = (const char *)base[r];
         pf.lines[r] = base[r] ? (bytes[r] + 127) / 128 : 0;
-        most = std::max(most, pf.lines[r]);
+        *most = std::max(*most, pf.lines[r]);
     }
+    return pf;
+}
+
+nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cudaStream_t st) {
+    const int ns = c->S_host * NB_SCA;
+    NbTraceScope tr(c, NB_TRACE_GATHER, st);
+    c->n_launches++;
+    c->xq_cur = nullptr;  // the positions of this call go to the context's own array
+    long long most = 0;
+    const L2Prefetch pf = list_prefetch(c, &most);
     const long long threads = std::max<long long>(ns, most);
     k_gather<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ns, c->perm, x, c->img, c->q_s, c->box[0], c->box[1],
                                                                 c->box[2], c->xq, c->fs, e, vir, c->err, c->queue,
@@ -225,6 +252,37 @@ void nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, int n_sm,
 }
 
 int nb_force_blocks(int n_items) { return n_items; }  // rows of per-item partial sums
+
+// Sorted-layout mode: prep (zeroing, prefetch), the force kernel on the caller's
+// sorted positions and force array, and the fold of the energy / virial rows.
+nb_status nb_launch_forces_sorted(nb_ctx *c, unsigned flags, const float4 *xq, float4 *f, double *e, double *vir,
+                                  cudaStream_t st) {
+    const int ns = c->S_host * NB_SCA;
+    const bool red = flags & (NB_ENERGY | NB_VIRIAL);
+    double *ee = (flags & NB_ENERGY) ? e : nullptr, *vv = (flags & NB_VIRIAL) ? vir : nullptr;
+    long long most = 0;
+    const L2Prefetch pf = list_prefetch(c, &most);
+    const long long threads = std::max<long long>(ns, most);
+    c->xq_cur = xq;  // the prune and the counts read this call's positions
+    {
+        NbTraceScope tr(c, NB_TRACE_GATHER, st);
+        c->n_launches++;
+        k_prep_sorted<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ns, f, ee, vv, c->queue, pf);
+    }
+    SysView v = nb_make_view(c, f, ee, vv);
+    if (v.n_items > 0) {
+        NbTraceScope tr(c, NB_TRACE_FORCES, st);
+        nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
+        c->n_launches++;
+    }
+    if (red && v.n_items > 0) {  // fold the per-item rows (no forces to scatter)
+        c->n_launches++;
+        k_unsort<<<64, 256, 0, st>>>(0, c->inv, c->fs, nullptr, c->part, nb_force_blocks(v.n_items),
+                                     138.935458 / c->eps_r, ee, vv);
+    }
+    NB_CUDA_TRY(cudaGetLastError());
+    return NB_OK;
+}
 
 nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, double *vir, cudaStream_t st,
                            bool fused_prune) {

@@ -64,9 +64,10 @@ struct SysView {
     float k_rf, c_rf, c_rf_lo;  // c_rf as a float pair (c_rf + c_rf_lo)
     float ew_s;      // beta^2 / ZMAX^2
     float ew_beta3;  // beta^3
-    float ew_beta;   // beta
+    float ew_beta;   // beta (float pair with ew_beta_lo)
     float ew_shift;  // erfc(beta rc)/rc (without the Coulomb constant)
-    float ew_beta2;  // beta^2
+    float ew_beta2;  // beta^2 (float pair with ew_beta2_lo)
+    float ew_beta_lo, ew_beta2_lo;  // beta - (float)beta, beta^2 - (float)beta^2
     float ew_2bsp;   // 2 beta / sqrt(pi)
     float rc6inv, rc12inv;
     int *queue;  // work-item counter of the persistent force kernel (zeroed by the gather)
@@ -146,6 +147,7 @@ struct nb_ctx {
     int N_cap = 0;
     // sorted layout
     float4 *xq = nullptr;
+    const float4 *xq_cur = nullptr;  // positions of the last force call: xq, or the caller's (sorted mode)
     int *type_s = nullptr, *perm = nullptr, *inv = nullptr, *sc_col = nullptr;
     float *q_s = nullptr;
     float4 *bb = nullptr;   // [S_cap*8*2]
@@ -218,6 +220,8 @@ nb_status nb_cuda_status(cudaError_t e);
     } while (0)
 
 nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir);
+// positions of the last force call (sorted mode: the caller's array), else of the last gather or sort
+inline const float4 *nb_cur_xq(const nb_ctx *c) { return c->xq_cur ? c->xq_cur : c->xq; }
 int nb_force_blocks(int n_items);
 
 // launchers (one per translation unit)
@@ -229,6 +233,8 @@ nb_status nb_launch_prune_compact_all(nb_ctx *c, cudaStream_t st);
 nb_status nb_ensure_inner(nb_ctx *c, cudaStream_t st);
 nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, double *vir,
                            cudaStream_t st, bool fused_prune = false);
+nb_status nb_launch_forces_sorted(nb_ctx *c, unsigned flags, const float4 *xq, float4 *f, double *e, double *vir,
+                                  cudaStream_t st);
 nb_status nb_launch_count(nb_ctx *c, int which, cudaStream_t st);
 nb_status nb_launch_export(nb_ctx *c, int which, long long *buf, long long cap, long long *count,
                            cudaStream_t st);

@@ -2,14 +2,19 @@
 //
 // Every other entry point works on a context whose device buffers are
 // allocated by nb_create / nb_grid_sort / nb_pairlist_build.  Some callers
-// cannot call cudaMalloc at all: code that runs while a stream is being
-// captured into a CUDA graph (allocation is not permitted there), code inside a
-// framework whose device memory is owned by another allocator, or latency-
-// critical code that cannot afford cudaMalloc/cudaFree, which may synchronise
-// the device.  nb_forces_small_noalloc serves them: the caller passes only
-// inputs and outputs, and the kernel's scratch (wrapped positions and types,
-// and per-block partial sums of the energies and the virial) lives in a
+// cannot call cudaMalloc at all: code inside a framework whose device memory is
+// owned by another allocator (a caching allocator or a pool reserved up front),
+// code that is not allowed to allocate after its start-up, or latency-critical
+// code that cannot afford cudaMalloc/cudaFree, which may synchronise the
+// device.  nb_forces_small_noalloc serves them: the caller passes only inputs
+// and outputs, and the kernel's scratch (wrapped positions and types, a status
+// word, and per-block partial sums of the energies and the virial) lives in a
 // file-scope static device array, so the call allocates nothing.
+//
+// Inputs that only the device can check (atom types, exclusion row lengths) are
+// validated by the first kernel; an invalid atom sets the status word, and then
+// every output of the call is NaN (forces, energies, virial) instead of a
+// silently wrong number.
 //
 // The kernel is a variant of the cluster pair force kernel for systems small
 // enough to evaluate all pairs: each thread owns one i-atom and walks a chunk
@@ -34,11 +39,13 @@ constexpr int kNaMaxBlocks = (NB_NOALLOC_MAX_ATOMS + kNaThreads - 1) / kNaThread
 constexpr int kNaRow = 11;        // E_LJ, E_C, 9 virial components
 
 // The scratch: wrapped positions (x, y, z, q) and types of up to
-// NB_NOALLOC_MAX_ATOMS atoms, then one row of partial sums per block.  Every
-// call overwrites the parts it reads, so nothing has to start at zero.
+// NB_NOALLOC_MAX_ATOMS atoms, the status word (non-zero: an atom failed the
+// input checks; cleared by every call before its first kernel), then one row of
+// partial sums per block.  Every call overwrites the other parts it reads.
 struct NaScratch {
     float4 xq[NB_NOALLOC_MAX_ATOMS];
     int type[NB_NOALLOC_MAX_ATOMS];
+    int bad;
     double rows[kNaMaxBlocks * kNaRow];
 };
 static __device__ __align__(256) NaScratch g_na_scratch;
@@ -60,9 +67,20 @@ struct NaArgs {
     NaScratch *scr;  // device address of g_na_scratch
 };
 
+// Wrap the positions into the box, copy charges and types, zero the forces, and
+// check what the host cannot: each type must lie in [0, T) and each exclusion
+// row must have 0..NB_MAX_EXCL entries (an atom's own partners are kept in
+// registers by the force kernel, so a longer row cannot be honoured).
 __global__ void k_na_prep(const NaArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    const int t = a.type[i];
+    bool ok = t >= 0 && t < a.T;
+    if (a.excl_off) {
+        const int lo = a.excl_off[i], hi = a.excl_off[i + 1];
+        ok = ok && lo >= 0 && hi >= lo && hi - lo <= NB_MAX_EXCL;
+    }
+    if (!ok) atomicOr(&a.scr->bad, 1);
     float w[3];
     for (int k = 0; k < 3; k++) {
         const float xs = a.x[3 * i + k];
@@ -73,7 +91,7 @@ __global__ void k_na_prep(const NaArgs a) {
         a.f[3 * i + k] = 0.f;
     }
     a.scr->xq[i] = make_float4(w[0], w[1], w[2], a.q[i]);
-    a.scr->type[i] = a.type[i];
+    a.scr->type[i] = ok ? t : 0;
 }
 
 template <int COUL, bool EN>
@@ -83,11 +101,15 @@ __global__ void __launch_bounds__(kNaThreads) k_na_forces(const NaArgs a) {
     __shared__ float2 s_lj[NB_NOALLOC_MAX_TYPES * NB_NOALLOC_MAX_TYPES];
     __shared__ float4 s_lje[NB_NOALLOC_MAX_TYPES * NB_NOALLOC_MAX_TYPES];
     __shared__ double s_red[kNaThreads / 32][kNaRow];
+    const int i = blockIdx.x * kNaThreads + threadIdx.x;
+    if (a.scr->bad) {  // some atom failed the input checks: every force is NaN
+        if (blockIdx.y == 0 && i < a.n) a.f[3 * i] = a.f[3 * i + 1] = a.f[3 * i + 2] = __int_as_float(0x7fffffff);
+        return;  // (uniform over the grid: no block reaches the barriers below)
+    }
     for (int t = threadIdx.x; t < a.T * a.T; t += blockDim.x) {
         s_lj[t] = a.lj[t];
         s_lje[t] = a.lje[t];
     }
-    const int i = blockIdx.x * kNaThreads + threadIdx.x;
     const bool active = i < a.n;
     float4 xi = active ? a.scr->xq[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int ti = active ? a.scr->type[i] * a.T : 0;
@@ -169,7 +191,9 @@ __global__ void k_na_finish(const NaArgs a, int n_rows) {
     const int k = threadIdx.x;
     if (k >= kNaRow) return;
     double s = 0.0;
-    for (int r = 0; r < n_rows; r++) s += a.scr->rows[r * kNaRow + k];
+    if (a.scr->bad) s = __longlong_as_double(0x7ff8000000000000ll);  // invalid input: NaN outputs
+    else
+        for (int r = 0; r < n_rows; r++) s += a.scr->rows[r * kNaRow + k];
     if (k == 0) {
         if (a.e) a.e[0] = s;
     } else if (k == 1) {
@@ -179,7 +203,10 @@ __global__ void k_na_finish(const NaArgs a, int n_rows) {
     }
 }
 
-// device address of the scratch, looked up once per device (with that device current)
+// device address of the scratch, looked up once per device (with that device
+// current) and kept for the life of the process: after cudaDeviceReset the
+// module is loaded again and this address is stale, so the entry point must not
+// be used on a device after resetting it
 std::mutex g_na_mutex;
 NaScratch *g_na_addr[64] = {nullptr};
 
@@ -248,6 +275,8 @@ extern "C" nb_status nb_forces_small_noalloc(const nb_params *p, const float *x_
     a.v.kept = nullptr;
     a.v.rin2 = 0.f;
     a.v.ew_beta2 = (float)(p->beta * p->beta);
+    a.v.ew_beta_lo = (float)(p->beta - (double)a.v.ew_beta);
+    a.v.ew_beta2_lo = (float)(p->beta * p->beta - (double)a.v.ew_beta2);
     a.v.ew_2bsp = (float)(2.0 * p->beta / sqrt(M_PI));
     a.v.rc6inv = (float)rc6inv;
     a.v.rc12inv = (float)(rc6inv * rc6inv);
@@ -278,10 +307,11 @@ extern "C" nb_status nb_forces_small_noalloc(const nb_params *p, const float *x_
     a.e = (flags & NB_ENERGY) ? e_dev : nullptr;
     a.vir = (flags & NB_VIRIAL) ? vir_dev : nullptr;
     a.scr = scr;
-    // ---- launches
+    // ---- launches (the status word starts each call at zero)
     cudaStream_t st = (cudaStream_t)stream;
     const bool en = flags & (NB_ENERGY | NB_VIRIAL);
     const dim3 grid((n + kNaThreads - 1) / kNaThreads, kNaJSplit);
+    NB_CUDA_TRY(cudaMemsetAsync(&scr->bad, 0, sizeof(int), st));
     k_na_prep<<<(n + 255) / 256, 256, 0, st>>>(a);
     if (p->coulomb == NB_COULOMB_RF) {
         if (en) k_na_forces<NB_COULOMB_RF, true><<<grid, kNaThreads, 0, st>>>(a);

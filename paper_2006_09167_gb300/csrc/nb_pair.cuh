@@ -42,18 +42,32 @@ __device__ __forceinline__ float ew_expm(float x) {
     return p * __int_as_float((127 - (int)n) << 23);
 }
 
-// X(z) = exp(z^2) erfc(z), rational in t = z / ZMAX
+// Reciprocal of q > 0 within about half an ulp: the hardware approximation
+// refined by one Newton step on the FMA residual.  The energy kernels divide by
+// it in X(z); the bare approximation (a fast division) carries a rounding bias
+// that varies with z, and the Coulomb energy of water -- a sum whose terms cancel
+// about 3000-fold -- turned that into a relative energy error of 2e-6.
+__device__ __forceinline__ float rcp_refined(float q) {
+    const float r = __fdividef(1.0f, q);
+    return fmaf(r, fmaf(-q, r, 1.0f), r);
+}
+
+// X(z) = exp(z^2) erfc(z), a (6,6) rational in t = z / ZMAX
 __device__ __forceinline__ float ew_x(float z) {
     const float t = z * (1.0f / NB_EW_ZMAX);
-    float p = fmaf(NB_EW_XP4, t, NB_EW_XP3);
+    float p = fmaf(NB_EW_XP6, t, NB_EW_XP5);
+    p = fmaf(p, t, NB_EW_XP4);
+    p = fmaf(p, t, NB_EW_XP3);
     p = fmaf(p, t, NB_EW_XP2);
     p = fmaf(p, t, NB_EW_XP1);
     p = fmaf(p, t, NB_EW_XP0);
-    float q = fmaf(NB_EW_XQ4, t, NB_EW_XQ3);
+    float q = fmaf(NB_EW_XQ6, t, NB_EW_XQ5);
+    q = fmaf(q, t, NB_EW_XQ4);
+    q = fmaf(q, t, NB_EW_XQ3);
     q = fmaf(q, t, NB_EW_XQ2);
     q = fmaf(q, t, NB_EW_XQ1);
     q = fmaf(q, t, 1.0f);
-    return __fdividef(p, q);
+    return p * rcp_refined(q);
 }
 
 // Packed FP32 (sm_100 and later): one FFMA2 / FMUL2 / FADD2 instruction performs
@@ -101,15 +115,21 @@ __device__ __forceinline__ float2 ew_expm2(float2 x) {
 
 __device__ __forceinline__ float2 ew_x2(float2 z) {
     const float2 t = pmul(z, p2(1.0f / NB_EW_ZMAX));
-    float2 p = pfma(p2(NB_EW_XP4), t, p2(NB_EW_XP3));
+    float2 p = pfma(p2(NB_EW_XP6), t, p2(NB_EW_XP5));
+    p = pfma(p, t, p2(NB_EW_XP4));
+    p = pfma(p, t, p2(NB_EW_XP3));
     p = pfma(p, t, p2(NB_EW_XP2));
     p = pfma(p, t, p2(NB_EW_XP1));
     p = pfma(p, t, p2(NB_EW_XP0));
-    float2 q = pfma(p2(NB_EW_XQ4), t, p2(NB_EW_XQ3));
+    float2 q = pfma(p2(NB_EW_XQ6), t, p2(NB_EW_XQ5));
+    q = pfma(q, t, p2(NB_EW_XQ4));
+    q = pfma(q, t, p2(NB_EW_XQ3));
     q = pfma(q, t, p2(NB_EW_XQ2));
     q = pfma(q, t, p2(NB_EW_XQ1));
     q = pfma(q, t, p2(1.0f));
-    return make_float2(__fdividef(p.x, q.x), __fdividef(p.y, q.y));
+    float2 r = make_float2(__fdividef(1.0f, q.x), __fdividef(1.0f, q.y));  // rcp_refined per component
+    r = pfma(r, pfma(pneg(q), r, p2(1.0f)), r);
+    return pmul(p, r);
 }
 
 // Periodic shift of a work item split between the two sides of each pair so
@@ -198,9 +218,13 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
         fc = qq * fmaf(rinv, rinv2, -2.0f * v.k_rf);
     } else if (COUL == NB_COULOMB_EWALD) {
         if (EN) {
-            // one exp(-z^2) serves the energy, erfc(z) = exp(-z^2) X(z), and the force
-            const float ex = ew_expm(r2 * v.ew_beta2);
-            erfcz = ex * ew_x(v.ew_beta * (r2 * rinv));
+            // one exp(-z^2) serves the energy, erfc(z) = exp(-z^2) X(z), and the force;
+            // z = beta r and z^2 = beta^2 r^2 take beta and beta^2 as float pairs, so
+            // their FP32 rounding leaves no error that grows with z (each pair of the
+            // energy sum then carries only unbiased roundings)
+            const float r = r2 * rinv;
+            const float ex = ew_expm(fmaf(r2, v.ew_beta2, r2 * v.ew_beta2_lo));
+            erfcz = ex * ew_x(fmaf(v.ew_beta, r, v.ew_beta_lo * r));
             fc = qq * rinv2 * fmaf(erfcz, rinv, v.ew_2bsp * ex);
         } else {
             fc = qq * fmaf(rinv, rinv2, -v.ew_beta3 * ew_h(r2 * v.ew_s));
@@ -256,8 +280,9 @@ __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__re
         fc = pmul(qq, pfma(rinv, rinv2, p2(-2.0f * v.k_rf)));
     } else if (COUL == NB_COULOMB_EWALD) {
         if (EN) {
-            const float2 ex = ew_expm2(pmul(r2, p2(v.ew_beta2)));
-            erfcz = pmul(ex, ew_x2(pmul(p2(v.ew_beta), pmul(r2, rinv))));
+            const float2 r = pmul(r2, rinv);
+            const float2 ex = ew_expm2(pfma(r2, p2(v.ew_beta2), pmul(r2, p2(v.ew_beta2_lo))));
+            erfcz = pmul(ex, ew_x2(pfma(p2(v.ew_beta), r, pmul(p2(v.ew_beta_lo), r))));
             fc = pmul(pmul(qq, rinv2), pfma(erfcz, rinv, pmul(p2(v.ew_2bsp), ex)));
         } else {
             fc = pmul(qq, pfma(rinv, rinv2, pmul(p2(-v.ew_beta3), ew_h2(pmul(r2, p2(v.ew_s))))));

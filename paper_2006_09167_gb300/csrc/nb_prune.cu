@@ -236,7 +236,7 @@ nb_status nb_launch_prune(nb_ctx *c, float r_in, int part, int n_parts, cudaStre
     a.n_parts = n_parts;
     a.items = c->items;
     a.cj_outer = c->cj_outer;
-    a.xq = c->xq;
+    a.xq = nb_cur_xq(c);
     box_split(c, a.Lhi, a.Llo);
     // a hair wider than r_in so that FP32 rounding never drops a pair the FP64 definition keeps
     float re = r_in * (1.0f + 2e-6f);
@@ -297,7 +297,7 @@ nb_status nb_launch_count(nb_ctx *c, int which, cudaStream_t st) {
     c->n_launches++;
     k_count<<<(c->n_items + kPW - 1) / kPW, kPW * 32, 0, st>>>(
         c->n_items, c->items, which == NB_LIST_INNER ? c->inner_len : nullptr,
-        which == NB_LIST_INNER ? c->cj_inner : c->cj_outer, c->masks, c->xq, hi[0], hi[1], hi[2], lo[0], lo[1],
+        which == NB_LIST_INNER ? c->cj_inner : c->cj_outer, c->masks, nb_cur_xq(c), hi[0], hi[1], hi[2], lo[0], lo[1],
         lo[2], rc * rc, reinterpret_cast<unsigned long long *>(c->diag));
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;

@@ -80,16 +80,7 @@ __device__ __forceinline__ bool vjp_pair(const VjpView &v, const float4 *__restr
         const float r = r2 * rinv;
         const float z = sv.ew_beta * r;
         const float ez = __expf(-z * z);
-        const float t = z * (1.0f / NB_EW_ZMAX);
-        float xp = fmaf(NB_EW_XP4, t, NB_EW_XP3);
-        xp = fmaf(xp, t, NB_EW_XP2);
-        xp = fmaf(xp, t, NB_EW_XP1);
-        xp = fmaf(xp, t, NB_EW_XP0);
-        float xq = fmaf(NB_EW_XQ4, t, NB_EW_XQ3);
-        xq = fmaf(xq, t, NB_EW_XQ2);
-        xq = fmaf(xq, t, NB_EW_XQ1);
-        xq = fmaf(xq, t, 1.0f);
-        const float ec = ez * __fdividef(xp, xq);
+        const float ec = ez * ew_x(z);
         const float ex = v.two_beta_sqrtpi * ez;
         psi = f * fmaf(ec, rinv, ex) * rinv2;
         dpsi = f * (-3.f * ec * rinv2 * rinv2 * rinv - ex * fmaf(3.f, rinv2 * rinv2, 2.f * sv.ew_beta * sv.ew_beta * rinv2));
@@ -421,6 +412,7 @@ nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, f
     const int ns = c->S_host * NB_SCA;
     const int npar = 2 * c->T * c->T;
     const int nthr = ns > npar ? ns : npar;
+    c->xq_cur = nullptr;  // the adjoint gathers its positions into the context's own array
     k_vjp_gather<<<(nthr + 255) / 256, 256, 0, st>>>(ns, c->perm, x, c->img, c->q_s, gF, c->box[0], c->box[1],
                                                       c->box[2], c->xq, c->gfs, c->gxs, c->gqs, c->gpar, npar,
                                                       c->err, c->queue);

@@ -173,7 +173,8 @@ def csr_from_pairs(n: int, pairs: np.ndarray):
     if pairs.size:
         assert np.all(pairs[:, 0] != pairs[:, 1])
         both = np.concatenate([pairs, pairs[:, ::-1]])
-        both = np.unique(both, axis=0)
+        key = np.unique(both[:, 0] * np.int64(n) + both[:, 1])  # sorted by (i, j), duplicates removed
+        both = np.stack([key // n, key % n], 1)
     else:
         both = np.zeros((0, 2), dtype=np.int64)
     counts = np.bincount(both[:, 0], minlength=n)
@@ -362,6 +363,7 @@ class _Grid:
         self.cap = cap
         self.slots = -np.ones((int(np.prod(self.nc)), cap), dtype=np.int64)
         self.fill = np.zeros(int(np.prod(self.nc)), dtype=np.int64)
+        self.fill_max = 0  # upper bound of fill (never lowered: extra slots are empty, -1)
         self.pos = []
 
     def _cid(self, c):
@@ -377,7 +379,7 @@ class _Grid:
                 for a in range(0, p.shape[0], chunk)])
         c = np.floor(p / self.cell).astype(int)
         offs = np.array([(a, b, d) for a in (-1, 0, 1) for b in (-1, 0, 1) for d in (-1, 0, 1)])
-        used = max(1, int(self.fill.max()))
+        used = max(1, self.fill_max)
         cand = self.slots[self._cid(c[:, None, :] + offs[None])][:, :, :used]  # [k,27,used]
         cand = cand.reshape(p.shape[0], -1)
         valid = cand >= 0
@@ -409,6 +411,7 @@ class _Grid:
                 raise RuntimeError("generator grid cell overflow")
             self.slots[c, f] = i
             self.fill[c] = f + 1
+            self.fill_max = max(self.fill_max, int(f) + 1)
 
 
 def polymer_water_box(seed: int = 3, n_chain: int = 1125, chain_len: int = 200,

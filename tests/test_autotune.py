@@ -39,7 +39,7 @@ def test_tune_on_gpu_gives_a_valid_correct_configuration(tmp_path):
         pytest.skip("no CUDA device")
     import oracle
     from paper_2006_09167_gb300 import api
-    from helpers import TOL_F, rms_rel
+    from helpers import assert_forces
     s = synth.water_box(3375, 4.66, seed=91, rc=1.0, rlist=1.1, r_in=1.03)
     x = torch.tensor(s.x, device="cuda")
     v = torch.tensor(synth.maxwell_boltzmann(s, 300.0, seed=1), dtype=torch.float32, device="cuda")
@@ -53,7 +53,7 @@ def test_tune_on_gpu_gives_a_valid_correct_configuration(tmp_path):
     ctx.nb_set_split(res["split"])
     ctx.build(x, s.box)
     f, e, w = ctx.forces(x, energy=True, virial=True)
-    assert rms_rel(f.cpu().numpy(), oracle.celllist(s)["F"]) < TOL_F
+    assert_forces(f.cpu().numpy(), oracle.celllist(s))
 
 
 @pytest.mark.gpu

@@ -48,9 +48,13 @@ def expm(c, x):
 
 
 def xfun(c, z):
+    # the kernels refine the reciprocal of the denominator to about half an ulp: modelled
+    # here as the rounded quotient
     t = (z * f32(1.0 / c["NB_EW_ZMAX"])).astype(f32)
-    p = horner([c[f"NB_EW_XP{k}"] for k in range(5)], t)
-    q = horner([f32(1.0)] + [c[f"NB_EW_XQ{k}"] for k in range(1, 5)], t)
+    m = max(int(k[8:]) for k in c if k.startswith("NB_EW_XP"))
+    n = max(int(k[8:]) for k in c if k.startswith("NB_EW_XQ"))
+    p = horner([c[f"NB_EW_XP{k}"] for k in range(m + 1)], t)
+    q = horner([f32(1.0)] + [c[f"NB_EW_XQ{k}"] for k in range(1, n + 1)], t)
     return (p.astype(np.float64) / q).astype(f32)
 
 

@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 from paper_2006_09167_gb300 import synth
-from helpers import TOL_F, TOL_W, energy_tolerances, rel, rms_rel
+from helpers import ENERGY_ROWS, TOL_W, assert_forces, energy_budget, energy_tolerances, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -47,7 +47,7 @@ def test_batched_equals_plain(api, replicas):
     off = b.offsets
     for r, (fp, ep, wp) in enumerate(plain):
         fb = f[off[r]:off[r + 1]].cpu().numpy()
-        assert rms_rel(fb, fp.cpu().numpy()) < 1e-6
+        assert_forces(fb, fp.cpu().numpy(), tol_rms=1e-6, tol_atom=1e-5)
         assert rel(e[2 * r].item(), ep[0].item()) < 1e-9
         assert rel(e[2 * r + 1].item(), ep[1].item()) < 1e-9
         wb = w[9 * r:9 * r + 9].cpu().numpy()
@@ -79,7 +79,7 @@ def test_batched_oracle_parity_and_graph_replay(api, replicas):
         sysr = replicas[r]
         ref = oracle.celllist(sysr)
         tol_lj, tol_c = energy_tolerances(sysr, ref)
-        assert rms_rel(f[off[r]:off[r + 1]].cpu().numpy(), ref["F"]) < TOL_F
+        assert_forces(f[off[r]:off[r + 1]].cpu().numpy(), ref)
         assert rel(e[2 * r].item(), ref["E_lj"]) < tol_lj
         assert rel(e[2 * r + 1].item(), ref["E_c"]) < tol_c
 
@@ -119,18 +119,24 @@ def test_batched_256_replicas_full_size(api):
     assert all(c.nb_get_error() == 0 for c in ctxs)
     off = b.offsets
     fa, ea, wa = f.cpu().numpy(), e.cpu().numpy(), w.cpu().numpy()
-    worst = 0.0
+    worst = worst_atom = 0.0
+    worst_e = None
     for r, sysr in enumerate(reps):
         ref = oracle.celllist(sysr)
-        tol_lj, tol_c = energy_tolerances(sysr, ref)
-        ef = rms_rel(fa[off[r]:off[r + 1]], ref["F"])
+        b = energy_budget(sysr, ref)
+        ef, em = assert_forces(fa[off[r]:off[r + 1]], ref)
         worst = max(worst, ef)
-        assert ef < TOL_F, (r, ef)
-        assert rel(ea[2 * r], ref["E_lj"]) < tol_lj, r
-        assert rel(ea[2 * r + 1], ref["E_c"]) < tol_c, r
+        worst_atom = max(worst_atom, em)
+        el, ec = rel(ea[2 * r], ref["E_lj"]), rel(ea[2 * r + 1], ref["E_c"])
+        assert el < b["tol_lj"], r
+        assert ec < b["tol_c"], r
+        ratio = max(el / b["tol_lj"], ec / b["tol_c"])
+        if worst_e is None or ratio > worst_e[0]:
+            worst_e = (ratio, dict(name=f"256 replicas (worst: {r})", n=int(sysr.n), err_lj=el, err_c=ec, **b))
         wr = wa[9 * r:9 * r + 9].reshape(3, 3)
         assert np.sqrt(((wr - ref["W"]) ** 2).sum() / (ref["W"] ** 2).sum()) < TOL_W, r
-    print(f"256 replicas: worst force RMS rel {worst:.2e}")
+    ENERGY_ROWS.append(worst_e[1])
+    print(f"256 replicas: worst force RMS rel {worst:.2e}, worst per-atom {worst_atom:.2e} of the RMS force")
 
 
 def test_batch_requires_lists(api, replicas):

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_2006_09167_gb300 import synth
-from helpers import TOL_F, canonical_pairs, rms_rel
+from helpers import assert_forces, canonical_pairs
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -47,13 +47,13 @@ def test_rolling_prune_listset_parity(api):
             torch.cuda.synchronize()
             pairs = ctx.nb_debug_export_pairs(api.NB_LIST_INNER)
             ref = oracle.listset(s, pairs, x=xh)
-            assert rms_rel(f2.cpu().numpy(), ref["F"]) < TOL_F
+            assert_forces(f2.cpu().numpy(), ref)
             if t == 1:
                 # shortly after the build every pair inside rc is listed (the buffers cover
                 # the motion); later, with ballistic motion and no rebuild, pairs may be missed
                 plain = oracle.celllist(s, x=xh)
                 assert ref["npairs"] == plain["npairs"]
-                assert rms_rel(f2.cpu().numpy(), plain["F"]) < TOL_F
+                assert_forces(f2.cpu().numpy(), plain)
     assert ctx.nb_get_error() == 0
 
 

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import EPS32, TOL_F, energy_tolerances, rel, rms_rel
+from helpers import EPS32, TOL_F, assert_forces, energy_tolerances, rel
 from paper_2006_09167_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -59,7 +59,7 @@ def check(api, s, force_scale=None, energy_scale=None):
     if force_scale is not None:
         assert np.abs(f - ref["F"]).max() < TOL_F * force_scale, (f, ref["F"])
     elif np.abs(ref["F"]).max() > 0:
-        assert rms_rel(f, ref["F"]) < TOL_F, (f, ref["F"])
+        assert_forces(f, ref)
     else:
         assert np.all(f == 0)
     if energy_scale is not None:

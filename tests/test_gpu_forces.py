@@ -6,8 +6,8 @@ import pytest
 
 import oracle
 from paper_2006_09167_gb300 import synth
-from helpers import (TOL_E, TOL_F, TOL_NET, TOL_W, all_images_within, canonical_pairs, energy_tolerances, rel,
-                     rms_rel)
+from helpers import (TOL_NET, TOL_W, all_images_within, assert_forces, canonical_pairs, check_energies,
+                     rel)
 
 pytestmark = pytest.mark.gpu
 
@@ -33,12 +33,10 @@ def run_forces(api, s, energy=True, virial=True, x=None):
         (w.cpu().numpy() if w is not None else None)
 
 
-def check_parity(s, ref, f, e, w, x=None):
-    assert rms_rel(f, ref["F"]) < TOL_F
+def check_parity(s, ref, f, e, w, x=None, name=None):
+    assert_forces(f, ref)
     if e is not None:
-        tol_lj, tol_c = energy_tolerances(s, ref, x)
-        assert rel(e[0], ref["E_lj"]) < tol_lj
-        assert rel(e[1], ref["E_c"]) < tol_c
+        check_energies(name or s.name, s, ref, e, x)
     if w is not None:
         assert np.sqrt(((w - ref["W"]) ** 2).sum() / (ref["W"] ** 2).sum()) < TOL_W
     net = np.abs(f.astype(np.float64).sum(0)).max()
@@ -126,7 +124,15 @@ def test_forces_648_reaction_field(api):
     s = synth.water_648()
     _, f, e, w = run_forces(api, s)
     ref = oracle.brute(s)
-    check_parity(s, ref, f, e, w)
+    check_parity(s, ref, f, e, w, name="648 water, reaction field")
+
+
+def test_forces_24k_six_types(api):
+    # the differentiation box's forward evaluation (Ewald, six LJ types)
+    s = synth.water_24k_types()
+    _, f, e, w = run_forces(api, s)
+    ref = oracle.celllist(s)
+    check_parity(s, ref, f, e, w, name="24k water, 6 LJ types, Ewald")
 
 
 @pytest.mark.parametrize("n_mol,box_len", [(1000, 3.1), (3375, 4.66)])
@@ -146,7 +152,7 @@ def test_forces_flags_agree(api):
     torch.cuda.synchronize()
     f0 = outs[0][0].cpu().numpy()
     for f, e, w in outs[1:]:
-        assert rms_rel(f.cpu().numpy(), f0) < 1e-6
+        assert_forces(f.cpu().numpy(), f0, tol_rms=1e-6, tol_atom=1e-5)
     assert outs[1][2] is not None and outs[2][1] is not None
 
 
@@ -175,13 +181,11 @@ def test_forces_96k_full_size_sampled(api):
     rng = np.random.default_rng(3)
     sub = np.sort(rng.choice(s.n, 4000, replace=False))
     ref = oracle.celllist(s, subset=sub)
-    assert rms_rel(f[sub], ref["F"]) < TOL_F
+    assert_forces(f[sub], ref)
     full = oracle.celllist(s)
-    tol_lj, tol_c = energy_tolerances(s, full)
-    assert rel(e[0], full["E_lj"]) < tol_lj
-    assert rel(e[1], full["E_c"]) < tol_c
+    check_energies("96k water, Ewald", s, full, e)
     assert np.sqrt(((w - full["W"]) ** 2).sum() / (full["W"] ** 2).sum()) < TOL_W
-    assert rms_rel(f, full["F"]) < TOL_F
+    assert_forces(f, full)
 
 
 def test_count_pairs_matches_oracle(api):
@@ -203,13 +207,11 @@ def test_forces_1p5M_polymer_water_full_size(api):
     sub = np.sort(np.concatenate([rng.choice(225000, 1500, replace=False),
                                   225000 + rng.choice(s.n - 225000, 1500, replace=False)]))
     ref = oracle.celllist(s, subset=sub)
-    assert rms_rel(f[sub], ref["F"]) < TOL_F
+    assert_forces(f[sub], ref)
     full = oracle.celllist(s)
-    tol_lj, tol_c = energy_tolerances(s, full)
-    assert rel(e[0], full["E_lj"]) < tol_lj
-    assert rel(e[1], full["E_c"]) < tol_c
+    check_energies("1.5M polymer + water, Ewald", s, full, e)
     assert np.sqrt(((w - full["W"]) ** 2).sum() / (full["W"] ** 2).sum()) < TOL_W
-    assert rms_rel(f, full["F"]) < TOL_F
+    assert_forces(f, full)
     net = np.abs(f.astype(np.float64).sum(0)).max()
     assert net < TOL_NET * np.abs(f).sum()
 

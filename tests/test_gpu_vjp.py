@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2006_09167_gb300 import synth
-from helpers import energy_tolerances, rms_rel
+from helpers import TOL_F_ATOM, energy_tolerances, max_atom_err, rms_rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -38,6 +38,7 @@ def gpu_vjp(api, s, gF, gE):
 
 def check(g, r):
     assert rms_rel(g["gx"], r["gx"]) < TOL_G
+    assert max_atom_err(g["gx"], r["gx"]) < TOL_F_ATOM
     assert rms_rel(g["gq"], r["gq"]) < TOL_G
     assert rms_rel(g["gc6"], r["gc6"]) < TOL_G
     assert rms_rel(g["gc12"], r["gc12"]) < TOL_G
@@ -95,12 +96,14 @@ def test_autograd_force_matching_loss(api):
     gF = (2.0 / (3 * s.n)) * (F.detach().cpu().numpy().astype(np.float64) - f_ref.cpu().numpy())
     r = oracle.vjp(s, gF, 1e-4)
     assert rms_rel(xq.grad.cpu().numpy(), r["gx"]) < TOL_G
+    assert max_atom_err(xq.grad.cpu().numpy(), r["gx"]) < TOL_F_ATOM
     assert rms_rel(q.grad.cpu().numpy(), r["gq"]) < TOL_G
     assert rms_rel(c6.grad.cpu().numpy(), r["gc6"]) < TOL_G
     assert rms_rel(c12.grad.cpu().numpy(), r["gc12"]) < TOL_G
     # forward values
     o = oracle.celllist(s)
     assert rms_rel(F.detach().cpu().numpy(), o["F"]) < 1e-5
+    assert max_atom_err(F.detach().cpu().numpy(), o["F"]) < TOL_F_ATOM
     tol_lj, tol_c = energy_tolerances(s, o)
     etot = o["E_lj"] + o["E_c"]
     bound = (tol_lj * abs(o["E_lj"]) + tol_c * abs(o["E_c"])) / abs(etot)
