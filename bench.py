@@ -196,25 +196,27 @@ def run_ours(args, rank, world, local_rank):
     # the headline runs in the sorted layout (nb_forces_sorted): between list builds the
     # positions, velocities and forces stay in the context's cluster order, as an MD engine
     # that integrates in its grid order keeps them; a rebuild goes through caller order
-    lay = {}
+    # caller-order arrays with one extra row that the padding slots map to (no boolean indexing,
+    # so no host synchronisation): zero velocity there, and a scratch row for positions
+    lay = {"v_ext": torch.cat([v, torch.zeros((1, 3), dtype=torch.float32, device=dev)]),
+           "x_ext": torch.empty((s.n + 1, 3), dtype=torch.float32, device=dev)}
 
     def export_sorted():
         ns = ctx.n_slots()
         if lay.get("ns") != ns:
             lay.update(ns=ns, xq=torch.empty((ns, 4), dtype=torch.float32, device=dev),
                        perm=torch.empty(ns, dtype=torch.int32, device=dev),
-                       f=torch.empty((ns, 4), dtype=torch.float32, device=dev))
+                       f=torch.empty((ns, 4), dtype=torch.float32, device=dev),
+                       v4=torch.zeros((ns, 4), dtype=torch.float32, device=dev))
         ctx.nb_sorted_export(lay["xq"], lay["perm"])
-        valid = lay["perm"] >= 0
-        idx = lay["perm"].clamp(min=0).long()
+        lay["idx"] = torch.where(lay["perm"] >= 0, lay["perm"], s.n).long()
         # velocities as (vx, vy, vz, 0) per slot: the update is one contiguous add over the slots
         # that leaves the charges (w) and the padding slots as they are
-        v4 = torch.zeros((ns, 4), dtype=torch.float32, device=dev)
-        v4[:, :3] = torch.where(valid[:, None], v.index_select(0, idx), torch.zeros((), device=dev))
-        lay["v4"], lay["valid"], lay["idx"] = v4, valid, idx
+        lay["v4"][:, :3] = lay["v_ext"].index_select(0, lay["idx"])
 
     def to_caller():
-        x.index_copy_(0, lay["idx"][lay["valid"]], lay["xq"][lay["valid"], :3])
+        lay["x_ext"].index_copy_(0, lay["idx"], lay["xq"][:, :3])
+        x.copy_(lay["x_ext"][:s.n])
 
     def rebuild():
         if args.caller_order:

@@ -275,10 +275,11 @@ nb_status nb_launch_forces_sorted(nb_ctx *c, unsigned flags, const float4 *xq, f
         nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
         c->n_launches++;
     }
-    if (red && v.n_items > 0) {  // fold the per-item rows (no forces to scatter)
+    if (red && v.n_items > 0) {  // fold the per-item rows (no forces to scatter): about one row per thread
+        const int n_part = nb_force_blocks(v.n_items);
         c->n_launches++;
-        k_unsort<<<64, 256, 0, st>>>(0, c->inv, c->fs, nullptr, c->part, nb_force_blocks(v.n_items),
-                                     138.935458 / c->eps_r, ee, vv);
+        k_unsort<<<std::min(1024, (n_part + 22) / 23), 256, 0, st>>>(0, c->inv, c->fs, nullptr, c->part, n_part,
+                                                                    138.935458 / c->eps_r, ee, vv);
     }
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;

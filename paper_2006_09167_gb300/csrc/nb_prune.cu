@@ -34,8 +34,12 @@ struct PruneArgs {
 //    i-atom t of every i-cluster) and writes each entry's surviving mask byte;
 //  k_prune_compact: one warp per item of this part copies the entries whose mask
 //    survived, in their original order, into the inner list.
+// When no item has more than one chunk (work items of at most 16 outer entries,
+// the usual split), the warp that prunes an item also compacts it (COMPACT):
+// one launch, and no round trip of the masks through memory.
 constexpr int kPruneChunk = 16;
 
+template <bool COMPACT>
 __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunks_per_item) {
     __shared__ float4 s_xi[kPW][NB_SCA];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -45,7 +49,10 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunk
     if (item >= a.n_items) return;
     const int4 it = a.items[item];
     const int e_begin = (int)(w % chunks_per_item) * kPruneChunk;
-    if (e_begin >= it.w) return;
+    if (e_begin >= it.w) {
+        if (COMPACT && lane == 0) a.inner_len[item] = 0;
+        return;
+    }
     const int e_end = min(it.w, e_begin + kPruneChunk);
     const int si = it.x, sidx = it.y, j0 = it.z;
     const ShiftSplit sh = make_shift(sidx, a.Lhi, a.Llo);
@@ -55,6 +62,7 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunk
     }
     __syncwarp();
     const int g = lane >> 3, t = lane & 7;
+    int cnt = 0;  // COMPACT: entries kept so far
     for (int e0 = e_begin; e0 < e_end; e0 += 4) {
         const int e = e0 + g;
         const bool valid = e < e_end;
@@ -91,8 +99,19 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunk
         kept |= __shfl_xor_sync(full, kept, 1);
         kept |= __shfl_xor_sync(full, kept, 2);
         kept |= __shfl_xor_sync(full, kept, 4);
-        if (t == 0 && valid) a.kept[j0 + e] = (unsigned short)kept;
+        if (COMPACT) {
+            // lane 0 of each group holds its entry's masks; entries keep their order
+            const bool keep = t == 0 && valid && kept != 0;
+            const unsigned kb = __ballot_sync(full, keep);
+            if (keep)
+                a.cj_inner[j0 + cnt + __popc(kb & ((1u << lane) - 1))] =
+                    make_int2(ent.x | ((kept >> 8) << 24), (ent.y & ~0xff) | (kept & 0xff));
+            cnt += __popc(kb);
+        } else if (t == 0 && valid) {
+            a.kept[j0 + e] = (unsigned short)kept;
+        }
     }
+    if (COMPACT && lane == 0) a.inner_len[item] = cnt;
 }
 
 __global__ void __launch_bounds__(kPW * 32) k_prune_compact(PruneArgs a) {
@@ -250,8 +269,13 @@ nb_status nb_launch_prune(nb_ctx *c, float r_in, int part, int n_parts, cudaStre
     NbTraceScope tr(c, NB_TRACE_PRUNE, st);
     c->n_launches += 2;
     const long long nwm = nw * chunks;
-    k_prune_masks<<<(unsigned)((nwm + kPW - 1) / kPW), kPW * 32, 0, st>>>(a, chunks);
-    k_prune_compact<<<(unsigned)((nw + kPW - 1) / kPW), kPW * 32, 0, st>>>(a);
+    if (chunks == 1) {  // an item fits one chunk: prune and compact in one pass
+        c->n_launches--;
+        k_prune_masks<true><<<(unsigned)((nwm + kPW - 1) / kPW), kPW * 32, 0, st>>>(a, chunks);
+    } else {
+        k_prune_masks<false><<<(unsigned)((nwm + kPW - 1) / kPW), kPW * 32, 0, st>>>(a, chunks);
+        k_prune_compact<<<(unsigned)((nw + kPW - 1) / kPW), kPW * 32, 0, st>>>(a);
+    }
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
 }

@@ -26,10 +26,14 @@ def api():
     return a
 
 
-def test_rolling_prune_listset_parity(api):
+@pytest.mark.parametrize("split", [16, 48])
+def test_rolling_prune_listset_parity(api, split):
+    # split 16: an item fits one prune chunk and is pruned and compacted in one pass;
+    # split 48: items of several chunks, masks first, then a compaction pass
     s = synth.water_box(1000, 3.1, seed=81, rc=1.0, rlist=1.1, r_in=1.05)
     v = synth.maxwell_boltzmann(s, 300.0, seed=3)
     ctx = api.NbContext.from_system(s)
+    ctx.nb_set_split(split)
     x = torch.tensor(s.x, device="cuda")
     ctx.build(x, s.box)
     vt = torch.tensor(v, dtype=torch.float32, device="cuda")

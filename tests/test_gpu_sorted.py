@@ -77,8 +77,10 @@ def test_sorted_md_loop(api):
     vel = torch.tensor(synth.maxwell_boltzmann(s, 300.0, seed=5), dtype=torch.float32, device="cuda")
     flags = api.NB_ENERGY | api.NB_VIRIAL
     ctx = api.NbContext.from_system(s)
-    ctx.build(torch.tensor(s.x, device="cuda"), s.box)
+    xc0 = torch.tensor(s.x, device="cuda")  # caller coordinates of the last build
+    ctx.build(xc0, s.box)
     xq, perm = ctx.nb_sorted_export()
+    xq0 = xq.clone()  # the sorted positions as exported (the images the sort chose)
     f = torch.empty_like(xq)
     e = torch.empty(2, dtype=torch.float64, device="cuda")
     w = torch.empty(9, dtype=torch.float64, device="cuda")
@@ -91,14 +93,18 @@ def test_sorted_md_loop(api):
     vs = sorted_velocities()
     for t in range(45):
         if t and t % 20 == 0:
-            ctx.build(_to_caller(xq, perm, s.n), s.box)
+            xc0 = _to_caller(xq, perm, s.n)
+            ctx.build(xc0, s.box)
             xq, perm = ctx.nb_sorted_export()  # the slot count may change with the new sort
+            xq0 = xq.clone()
             f = torch.empty_like(xq)
             vs = sorted_velocities()
         ctx.nb_forces_sorted(flags, xq, f, e, w)
         if t in (3, 21, 44):
             torch.cuda.synchronize()
-            xh = _to_caller(xq, perm, s.n).cpu().numpy()
+            # the exported pair shifts refer to the caller coordinates the sort was given: move
+            # those by the displacement since the export (the sorted images may differ by box vectors)
+            xh = (xc0 + _to_caller(xq - xq0, perm, s.n)).cpu().numpy()
             ref = oracle.listset(s, ctx.nb_debug_export_pairs(api.NB_LIST_INNER), x=xh)
             valid = perm >= 0
             fb = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
