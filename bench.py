@@ -774,10 +774,36 @@ def main_profile(args):
     """A short, fixed launch sequence for profilers: one build, then force evaluations
     (--profile-case forces: the 96k box; polymer_1.5m: the 1.5M-atom polymer/water box;
     batched: one batched launch over the 256 replicas; vjp: forward + adjoint calls on the
-    24k box with 6 LJ types) or PME + Ewald-correction calls (--profile-case pme)."""
+    24k box with 6 LJ types) or PME + Ewald-correction calls (--profile-case pme); step: the
+    headline MD step in the sorted layout on the 96k box, NSTLIST/2 untimed steps to reach a
+    mid-life list, then warmup + steps more (5 launches per step: prep, forces, energy fold,
+    prune, position update)."""
     import torch
     from paper_2006_09167_gb300 import api, synth
     flags = api.NB_ENERGY | api.NB_VIRIAL
+    if args.profile_case == "step":
+        s = synth.water_96k()
+        ctx = api.NbContext.from_system(s)
+        ctx.nb_set_split(args.split or 12)
+        x = torch.tensor(s.x, device="cuda")
+        v = torch.tensor(synth.maxwell_boltzmann(s, 300.0, seed=7), dtype=torch.float32, device="cuda")
+        ctx.build(x, s.box)
+        xq, perm = ctx.nb_sorted_export()
+        idx = torch.where(perm >= 0, perm, s.n).long()
+        v4 = torch.zeros_like(xq)
+        v4[:, :3] = torch.cat([v, torch.zeros((1, 3), device="cuda")]).index_select(0, idx)
+        f = torch.empty_like(xq)
+        e = torch.empty(2, dtype=torch.float64, device="cuda")
+        w = torch.empty(9, dtype=torch.float64, device="cuda")
+        for t in range(NSTLIST // 2 + args.warmup + args.steps):
+            ctx.nb_forces_sorted(flags, xq, f, e, w)
+            ctx.nb_prune_rolling(t % N_PARTS, N_PARTS)
+            xq.add_(v4, alpha=DT)
+        torch.cuda.synchronize()
+        assert ctx.nb_get_error() == 0
+        print(json.dumps({"profile_case": "spce_water_96k_ewald_sorted_step", "launches": ctx.nb_get_stats()["n_launches"],
+                          "steps": NSTLIST // 2 + args.warmup + args.steps}))
+        return
     if args.profile_case == "batched":
         reps = synth.replica_set()
         ctxs, xs = [], []
@@ -882,7 +908,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true",
                     help="profiling target: warmup + steps force evaluations (energy+virial) of the 96k box only")
-    ap.add_argument("--profile-case", choices=["forces", "pme", "polymer_1.5m", "batched", "vjp"], default="forces",
+    ap.add_argument("--profile-case", choices=["forces", "step", "pme", "polymer_1.5m", "batched", "vjp"],
+                    default="forces",
                     help="with --profile: the launch sequence to run")
     ap.add_argument("--split", type=int, default=0,
                     help="with --profile: the work-item split to build with (default: the library's)")

@@ -203,6 +203,14 @@ nb_status nb_forces_vjp(nb_ctx *ctx, const float *x_dev, const float *gF_dev, do
                         float *gx_dev, float *gq_dev, double *gc6_dev, double *gc12_dev,
                         void *stream);
 
+/* nb_forces_vjp with the energy weight read from device memory, gE_dev [1]
+ * (FP64), by the adjoint kernel itself: a caller whose gE is the output of an
+ * earlier kernel (an autograd backward pass) needs no host synchronisation to
+ * read it.  Same outputs and errors as nb_forces_vjp; gE_dev must stay valid
+ * until the call's work has run.  Asynchronous; never allocates. */
+nb_status nb_forces_vjp_dev(nb_ctx *ctx, const float *x_dev, const float *gF_dev, const double *gE_dev,
+                            float *gx_dev, float *gq_dev, double *gc6_dev, double *gc12_dev, void *stream);
+
 /* Batched evaluation of independent systems in one persistent launch
  * (Sec. VI ensembles sharing a GPU; tail balancing of Sec. V.F).  The batch
  * refers to (does not own) `n` contexts that already have pair lists and the

@@ -36,7 +36,7 @@ EXPORTED = [
     "nb_forces_batched", "nb_count_pairs", "nb_debug_export_pairs", "nb_debug_layout",
     "nb_get_stats", "nb_get_error", "nb_status_str", "nb_trace_enable", "nb_trace_read",
     "nb_forces_small_noalloc", "nb_set_split", "nb_pme_create", "nb_pme_destroy", "nb_pme_forces",
-    "nb_ewald_corrections", "nb_set_fused_prune", "nb_sorted_export", "nb_forces_sorted",
+    "nb_ewald_corrections", "nb_set_fused_prune", "nb_sorted_export", "nb_forces_sorted", "nb_forces_vjp_dev",
 ]
 NB_NOALLOC_MAX_ATOMS = 16384
 NB_NOALLOC_MAX_TYPES = 8
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
     lib.nb_forces.argtypes = [vp, ctypes.c_uint, vp, vp, vp, vp, vp]
     lib.nb_forces_vjp.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp]
     lib.nb_sorted_export.argtypes = [vp, vp, vp, vp]
+    lib.nb_forces_vjp_dev.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.nb_forces_sorted.argtypes = [vp, ctypes.c_uint, vp, vp, vp, vp, vp]
     lib.nb_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
     lib.nb_batch_destroy.argtypes = [vp]

@@ -127,6 +127,15 @@ class NbContext:
         check(self._lib.nb_forces(self.handle, ctypes.c_uint(flags), _dev(x, torch.float32, 3 * self.n, "x"),
                                   _dev(f, torch.float32, 3 * self.n, "f"), ep, vp, _stream(stream)), "nb_forces")
 
+    def nb_forces_vjp_dev(self, x, gF, gE: torch.Tensor, gx, gq, gc6, gc12, stream=None):
+        """nb_forces_vjp with gE a one-element float64 CUDA tensor (no host synchronisation)."""
+        tt = self.T * self.T
+        check(self._lib.nb_forces_vjp_dev(self.handle, _dev(x, torch.float32, 3 * self.n, "x"),
+                                          _dev(gF, torch.float32, 3 * self.n, "gF"), _dev(gE, torch.float64, 1, "gE"),
+                                          _dev(gx, torch.float32, 3 * self.n, "gx"),
+                                          _dev(gq, torch.float32, self.n, "gq"), _dev(gc6, torch.float64, tt, "gc6"),
+                                          _dev(gc12, torch.float64, tt, "gc12"), _stream(stream)), "nb_forces_vjp_dev")
+
     def n_slots(self) -> int:
         """Slots of the sorted layout (64 per super-cluster, padding included)."""
         return int(self.nb_get_stats()["n_slots"])
@@ -372,12 +381,14 @@ class _ForcesFn(torch.autograd.Function):
         nb = ctx.nbctx
         if gF is None:
             gF = torch.zeros((nb.n, 3), dtype=torch.float32, device=x.device)
-        ge = float(gE.item()) if gE is not None else 0.0
+        # the energy weight stays on the device: no host synchronisation in the backward pass
+        ge = (gE.detach().reshape(1).to(torch.float64) if gE is not None
+              else torch.zeros(1, dtype=torch.float64, device=x.device)).contiguous()
         gx = torch.empty((nb.n, 3), dtype=torch.float32, device=x.device)
         gq = torch.empty(nb.n, dtype=torch.float32, device=x.device)
         gc6 = torch.empty((nb.T, nb.T), dtype=torch.float64, device=x.device)
         gc12 = torch.empty((nb.T, nb.T), dtype=torch.float64, device=x.device)
-        nb.nb_forces_vjp(x.detach().contiguous(), gF.contiguous().to(torch.float32), ge, gx, gq, gc6, gc12)
+        nb.nb_forces_vjp_dev(x.detach().contiguous(), gF.contiguous().to(torch.float32), ge, gx, gq, gc6, gc12)
         return gx, gq, gc6.to(torch.float32), gc12.to(torch.float32), None
 
 

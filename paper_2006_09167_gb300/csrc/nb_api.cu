@@ -526,7 +526,15 @@ nb_status nb_forces_vjp(nb_ctx *c, const float *x_dev, const float *gF_dev, doub
     if (!isfinite(gE)) return NB_ERR_INVALID_ARG;
     if (!c->have_list) return NB_ERR_NOT_READY;
     if (nb_status s = nb_ensure_inner(c, (cudaStream_t)stream); s != NB_OK) return s;
-    return nb_launch_vjp(c, x_dev, gF_dev, gE, gx_dev, gq_dev, gc6_dev, gc12_dev, (cudaStream_t)stream);
+    return nb_launch_vjp(c, x_dev, gF_dev, gE, nullptr, gx_dev, gq_dev, gc6_dev, gc12_dev, (cudaStream_t)stream);
+}
+
+nb_status nb_forces_vjp_dev(nb_ctx *c, const float *x_dev, const float *gF_dev, const double *gE_dev, float *gx_dev,
+                            float *gq_dev, double *gc6_dev, double *gc12_dev, void *stream) {
+    if (!c || !x_dev || !gF_dev || !gE_dev || !gx_dev || !gq_dev || !gc6_dev || !gc12_dev) return NB_ERR_INVALID_ARG;
+    if (!c->have_list) return NB_ERR_NOT_READY;
+    if (nb_status s = nb_ensure_inner(c, (cudaStream_t)stream); s != NB_OK) return s;
+    return nb_launch_vjp(c, x_dev, gF_dev, 0.0, gE_dev, gx_dev, gq_dev, gc6_dev, gc12_dev, (cudaStream_t)stream);
 }
 
 nb_status nb_count_pairs(nb_ctx *c, int which, int64_t *n_within, int64_t *n_eval, void *stream) {

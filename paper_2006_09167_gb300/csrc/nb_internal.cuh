@@ -238,5 +238,5 @@ nb_status nb_launch_forces_sorted(nb_ctx *c, unsigned flags, const float4 *xq, f
 nb_status nb_launch_count(nb_ctx *c, int which, cudaStream_t st);
 nb_status nb_launch_export(nb_ctx *c, int which, long long *buf, long long cap, long long *count,
                            cudaStream_t st);
-nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, float *gx, float *gq,
-                        double *gc6, double *gc12, cudaStream_t st);
+nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, const double *gE_dev, float *gx,
+                        float *gq, double *gc6, double *gc12, cudaStream_t st);

@@ -41,7 +41,8 @@ struct VjpView {
     float4 *gx;        // sorted dL/dx accumulators
     float *gq;         // sorted dL/dq accumulators
     double *gpar;      // [2*T*T] unsymmetrised dL/dC6, dL/dC12
-    float gE;
+    float gE;          // the energy's weight, or
+    const double *gE_dev;  // read from device memory when not null (no host synchronisation)
     float two_beta_sqrtpi;  // 2 beta / sqrt(pi)
 };
 
@@ -52,10 +53,10 @@ struct VjpView {
 // whether the pair counts.
 template <int COUL>
 __device__ __forceinline__ bool vjp_pair(const VjpView &v, const float4 *__restrict__ lje, float3 d, float3 wv,
-                                         float qi, float qj, int tpair, bool bit, float3 &g, float &gqc, float &g6,
-                                         float &g12, int &tsym) {
+                                         float qi, float qj, int tpair, bool bit, float gE, float3 &g, float &gqc,
+                                         float &g6, float &g12, int &tsym) {
     const SysView &sv = v.s;
-    const float f = sv.coul_f, gE = v.gE;
+    const float f = sv.coul_f;
     float r2 = fmaf(d.z, d.z, fmaf(d.y, d.y, d.x * d.x));
     const bool in = bit && (r2 < sv.rc2);
     r2 = in ? r2 : sv.rc2;
@@ -120,7 +121,7 @@ __device__ __forceinline__ void add_par(float *p6, float *p12, int tp, int lane,
 // half masks, two pairs per lane where both j-halves are kept.
 template <int COUL, bool PRIV>
 __device__ __forceinline__ void vjp_item(const VjpView &v, int w, int nj, float4 *s_xi, float4 *s_gi, int *s_ti,
-                                         float *s_ga, const float4 *lje, float *p6, float *p12, int T) {
+                                         float *s_ga, const float4 *lje, float *p6, float *p12, int T, float gE) {
     const SysView &sv = v.s;
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
@@ -164,10 +165,10 @@ __device__ __forceinline__ void vjp_item(const VjpView &v, int w, int nj, float4
             int u0, u1;
             const bool in0 = vjp_pair<COUL>(v, lje, make_float3(xi.x - xj0.x, xi.y - xj0.y, xi.z - xj0.z),
                                             make_float3(gi.x - gj0.x, gi.y - gj0.y, gi.z - gj0.z), xi.w, xj0.w,
-                                            ta * T + tb0, b0, g0, q0, c60, c120, u0);
+                                            ta * T + tb0, b0, gE, g0, q0, c60, c120, u0);
             const bool in1 = vjp_pair<COUL>(v, lje, make_float3(xi.x - xj1.x, xi.y - xj1.y, xi.z - xj1.z),
                                             make_float3(gi.x - gj1.x, gi.y - gj1.y, gi.z - gj1.z), xi.w, xj1.w,
-                                            ta * T + tb1, b1, g1, q1, c61, c121, u1);
+                                            ta * T + tb1, b1, gE, g1, q1, c61, c121, u1);
             float *ga = s_ga + k * 128 + lane;
             ga[0] += g0.x + g1.x;
             ga[32] += g0.y + g1.y;
@@ -201,7 +202,7 @@ __device__ __forceinline__ void vjp_item(const VjpView &v, int w, int nj, float4
             int u;
             const bool in = vjp_pair<COUL>(v, lje, make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z),
                                            make_float3(gi.x - gj.x, gi.y - gj.y, gi.z - gj.z), xi.w, xj.w, ta * T + tb,
-                                           b, g, q, c6, c12, u);
+                                           b, gE, g, q, c6, c12, u);
             float *ga = s_ga + k * 128 + lane;
             ga[0] += g.x;
             ga[32] += g.y;
@@ -299,11 +300,12 @@ __global__ void __launch_bounds__(kVW * 32) k_vjp(VjpView v, int *queue) {
     }
     __syncthreads();
     const int n_warps = gridDim.x * kVW;
+    const float gE = v.gE_dev ? (float)*v.gE_dev : v.gE;
     int w = blockIdx.x * kVW + wib;
     while (w < sv.n_items) {
         const int nj = sv.inner_len[w];
         if (nj > 0) {
-            vjp_item<COUL, PRIV>(v, w, nj, s_xi[wib], s_gi[wib], s_ti[wib], s_ga[wib], s_lje, p6, p12, T);
+            vjp_item<COUL, PRIV>(v, w, nj, s_xi[wib], s_gi[wib], s_ti[wib], s_ga[wib], s_lje, p6, p12, T, gE);
             __syncwarp();
             for (int t = lane; t < TS; t += 32) {
                 float a = 0.f, b = 0.f;
@@ -406,8 +408,8 @@ void launch_vjp(const VjpView &v, int nb, size_t smem, int n_sm, int *queue, cud
 
 }  // namespace
 
-nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, float *gx, float *gq, double *gc6,
-                        double *gc12, cudaStream_t st) {
+nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, const double *gE_dev, float *gx,
+                        float *gq, double *gc6, double *gc12, cudaStream_t st) {
     if (c->T > kVjpMaxT) return NB_ERR_INVALID_ARG;
     const int ns = c->S_host * NB_SCA;
     const int npar = 2 * c->T * c->T;
@@ -423,6 +425,7 @@ nb_status nb_launch_vjp(nb_ctx *c, const float *x, const float *gF, double gE, f
     v.gq = c->gqs;
     v.gpar = c->gpar;
     v.gE = (float)gE;
+    v.gE_dev = gE_dev;
     v.two_beta_sqrtpi = (float)(2.0 * c->beta / sqrt(M_PI));
     c->n_launches += 2;
     if (v.s.n_items > 0) {

@@ -108,3 +108,31 @@ def test_autograd_force_matching_loss(api):
     etot = o["E_lj"] + o["E_c"]
     bound = (tol_lj * abs(o["E_lj"]) + tol_c * abs(o["E_c"])) / abs(etot)
     assert abs(E.item() - etot) / abs(etot) < bound
+
+
+def test_vjp_energy_weight_from_device_memory(api):
+    """nb_forces_vjp_dev reads gE on the device (no host synchronisation): the same gradients
+    as nb_forces_vjp given the same weight on the host."""
+    s = synth.water_box(1000, 3.1, seed=93, rc=1.0, rlist=1.1)
+    rng = np.random.default_rng(9)
+    gF = torch.tensor(rng.normal(size=(s.n, 3)), dtype=torch.float32, device="cuda")
+    ctx = api.NbContext.from_system(s)
+    x = torch.tensor(s.x, device="cuda")
+    ctx.build(x, s.box)
+    T = s.n_types
+    outs = []
+    for dev in (False, True):
+        gx = torch.empty((s.n, 3), device="cuda")
+        gq = torch.empty(s.n, device="cuda")
+        gc6 = torch.empty((T, T), dtype=torch.float64, device="cuda")
+        gc12 = torch.empty((T, T), dtype=torch.float64, device="cuda")
+        if dev:
+            ctx.nb_forces_vjp_dev(x, gF, torch.tensor([0.37], dtype=torch.float64, device="cuda"), gx, gq, gc6, gc12)
+        else:
+            ctx.nb_forces_vjp(x, gF, 0.37, gx, gq, gc6, gc12)
+        torch.cuda.synchronize()
+        outs.append([t.cpu().numpy() for t in (gx, gq, gc6, gc12)])
+    for a, b in zip(*outs):
+        assert rms_rel(b, a) < 1e-6
+    r = oracle.vjp(s, gF.cpu().numpy().astype(np.float64), 0.37)
+    check(dict(zip(("gx", "gq", "gc6", "gc12"), outs[1])), r)
