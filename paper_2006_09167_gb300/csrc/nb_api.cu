@@ -440,7 +440,7 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
         if ((s = dalloc(&c->mask_lanes, (size_t)cap * 32)) != NB_OK) return s;
         c->masks_cap = cap;
     }
-    const int nblk = nb_force_blocks(c->n_items) + 1;
+    const int nblk = nb_force_rows_max(c->n_items) + 1;
     if (nblk > c->part_cap) {
         int cap = nblk + nblk / 8 + 16;
         if ((s = dalloc(&c->part, (size_t)cap * 11)) != NB_OK) return s;

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
     // which the gather zeroed (no burst of atomics at launch)
     const int n_warps = gridDim.x * kFW;
     int w = blockIdx.x * kFW + wib;
+    double row = 0.0;  // lane < 11: FP64 sum of this warp's per-item partial sums
     while (w < v.n_items) {
         const int nj = PRUNE ? v.items[w].w : v.inner_len[w];
         KSum elj, ec;
@@ -62,15 +63,14 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
         if (nj > 0)
             process_item<COUL, EN, VIR, PRUNE>(v, w, nj, s_lj, s_lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
         if (EN || VIR) {
-            // FP32 warp reduction; one row of 11 partial sums per work item, reduced in
-            // FP64 by the unsort kernel (no block barrier, no same-address atomics)
+            // FP32 warp reduction of the item's sums, added in FP64 to the warp's row
             warp_reduce_outputs<EN, VIR>(elj, ec, vr);
             if (lane < 11) {
                 double val;
                 if (lane == 0) val = (double)elj.s - (double)elj.c;
                 else if (lane == 1) val = (double)ec.s - (double)ec.c;
                 else val = (double)vr[lane - 2];
-                v.part[(size_t)w * 11 + lane] = val;
+                row += val;
             }
         }
         __syncwarp();  // this warp's staging arrays are reused by its next item
@@ -78,6 +78,10 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
         if (lane == 0) claim = atomicAdd(v.queue, 1);
         w = n_warps + __shfl_sync(full, claim, 0);
     }
+    // one row of 11 partial sums per warp of the grid (zeros for a warp without items),
+    // folded by the unsort kernel: a few thousand rows instead of one per work item, and
+    // no block barrier or same-address atomics in this kernel
+    if ((EN || VIR) && lane < 11) v.part[(size_t)(blockIdx.x * kFW + wib) * 11 + lane] = row;
 }
 
 // Lines the force kernel will read from memory the gather does not write (inner
@@ -180,8 +184,9 @@ __global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__res
     }
 }
 
+// Returns the number of partial-sum rows the launch writes (one per warp).
 template <int COUL, bool EN, bool VIR, bool PRUNE = false>
-void launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
+int launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
     const size_t smem = (sizeof(float2) + (EN ? sizeof(float4) : 0)) * v.T * v.T;
     // the type-pair tables of many types, with the 17 KB of static staging arrays,
     // exceed the default 48 KB of shared memory (64 types: 96 KB of tables); opt in
@@ -194,6 +199,7 @@ void launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
         occ = 1;
     const int blocks = std::min((v.n_items + kFW - 1) / kFW, std::max(n_sm, 1) * occ);
     k_forces<COUL, EN, VIR, PRUNE><<<blocks, kFW * 32, smem, st>>>(v);
+    return blocks * kFW;
 }
 
 }  // namespace
@@ -231,27 +237,27 @@ nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cu
     return NB_OK;
 }
 
-void nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, int n_sm, cudaStream_t st) {
+// Returns the number of partial-sum rows written (one per warp of the launch).
+int nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, int n_sm, cudaStream_t st) {
     const bool en = flags & NB_ENERGY, vi = flags & NB_VIRIAL;
     if (coulomb == NB_COULOMB_RF) {
-        if (en && vi) launch_forces_t<NB_COULOMB_RF, true, true>(v, n_sm, st);
-        else if (en) launch_forces_t<NB_COULOMB_RF, true, false>(v, n_sm, st);
-        else if (vi) launch_forces_t<NB_COULOMB_RF, false, true>(v, n_sm, st);
-        else launch_forces_t<NB_COULOMB_RF, false, false>(v, n_sm, st);
+        if (en && vi) return launch_forces_t<NB_COULOMB_RF, true, true>(v, n_sm, st);
+        else if (en) return launch_forces_t<NB_COULOMB_RF, true, false>(v, n_sm, st);
+        else if (vi) return launch_forces_t<NB_COULOMB_RF, false, true>(v, n_sm, st);
+        else return launch_forces_t<NB_COULOMB_RF, false, false>(v, n_sm, st);
     } else if (coulomb == NB_COULOMB_EWALD) {
-        if (en && vi) launch_forces_t<NB_COULOMB_EWALD, true, true>(v, n_sm, st);
-        else if (en) launch_forces_t<NB_COULOMB_EWALD, true, false>(v, n_sm, st);
-        else if (vi) launch_forces_t<NB_COULOMB_EWALD, false, true>(v, n_sm, st);
-        else launch_forces_t<NB_COULOMB_EWALD, false, false>(v, n_sm, st);
+        if (en && vi) return launch_forces_t<NB_COULOMB_EWALD, true, true>(v, n_sm, st);
+        else if (en) return launch_forces_t<NB_COULOMB_EWALD, true, false>(v, n_sm, st);
+        else if (vi) return launch_forces_t<NB_COULOMB_EWALD, false, true>(v, n_sm, st);
+        else return launch_forces_t<NB_COULOMB_EWALD, false, false>(v, n_sm, st);
     } else {
-        if (en && vi) launch_forces_t<NB_COULOMB_NONE, true, true>(v, n_sm, st);
-        else if (en) launch_forces_t<NB_COULOMB_NONE, true, false>(v, n_sm, st);
-        else if (vi) launch_forces_t<NB_COULOMB_NONE, false, true>(v, n_sm, st);
-        else launch_forces_t<NB_COULOMB_NONE, false, false>(v, n_sm, st);
+        if (en && vi) return launch_forces_t<NB_COULOMB_NONE, true, true>(v, n_sm, st);
+        else if (en) return launch_forces_t<NB_COULOMB_NONE, true, false>(v, n_sm, st);
+        else if (vi) return launch_forces_t<NB_COULOMB_NONE, false, true>(v, n_sm, st);
+        else return launch_forces_t<NB_COULOMB_NONE, false, false>(v, n_sm, st);
     }
 }
 
-int nb_force_blocks(int n_items) { return n_items; }  // rows of per-item partial sums
 
 // Sorted-layout mode: prep (zeroing, prefetch), the force kernel on the caller's
 // sorted positions and force array, and the fold of the energy / virial rows.
@@ -270,13 +276,13 @@ nb_status nb_launch_forces_sorted(nb_ctx *c, unsigned flags, const float4 *xq, f
         k_prep_sorted<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ns, f, ee, vv, c->queue, pf);
     }
     SysView v = nb_make_view(c, f, ee, vv);
+    int n_part = 0;  // partial-sum rows written by the force kernel
     if (v.n_items > 0) {
         NbTraceScope tr(c, NB_TRACE_FORCES, st);
-        nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
+        n_part = nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
         c->n_launches++;
     }
-    if (red && v.n_items > 0) {  // fold the per-item rows (no forces to scatter): about one row per thread
-        const int n_part = nb_force_blocks(v.n_items);
+    if (red && n_part > 0) {  // fold the rows (no forces to scatter): about one row per thread
         c->n_launches++;
         k_unsort<<<std::min(1024, (n_part + 22) / 23), 256, 0, st>>>(0, c->inv, c->fs, nullptr, c->part, n_part,
                                                                     138.935458 / c->eps_r, ee, vv);
@@ -289,6 +295,7 @@ nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, doubl
                            bool fused_prune) {
     const bool red = flags & (NB_ENERGY | NB_VIRIAL);
     SysView v = nb_make_view(c, c->fs, (flags & NB_ENERGY) ? e : nullptr, (flags & NB_VIRIAL) ? vir : nullptr);
+    int n_part = 0;  // partial-sum rows written by the force kernel
     if (v.n_items > 0) {
         NbTraceScope tr(c, NB_TRACE_FORCES, st);
         if (fused_prune) {
@@ -298,18 +305,19 @@ nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, doubl
             v.kept = c->kept;
             const float re = (float)c->r_in * (1.0f + 2e-6f);  // as the separate prune pass
             v.rin2 = re * re;
-            if (c->coulomb == NB_COULOMB_RF) launch_forces_t<NB_COULOMB_RF, true, true, true>(v, c->n_sm, st);
-            else if (c->coulomb == NB_COULOMB_EWALD) launch_forces_t<NB_COULOMB_EWALD, true, true, true>(v, c->n_sm, st);
-            else launch_forces_t<NB_COULOMB_NONE, true, true, true>(v, c->n_sm, st);
+            if (c->coulomb == NB_COULOMB_RF) n_part = launch_forces_t<NB_COULOMB_RF, true, true, true>(v, c->n_sm, st);
+            else if (c->coulomb == NB_COULOMB_EWALD)
+                n_part = launch_forces_t<NB_COULOMB_EWALD, true, true, true>(v, c->n_sm, st);
+            else n_part = launch_forces_t<NB_COULOMB_NONE, true, true, true>(v, c->n_sm, st);
         } else {
-            nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
+            n_part = nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
         }
         c->n_launches++;
     }
     const int nb = (c->N + 255) / 256;
     c->n_launches++;
-    k_unsort<<<nb, 256, 0, st>>>(c->N, c->inv, c->fs, f, (red && v.n_items > 0) ? c->part : nullptr,
-                                 nb_force_blocks(v.n_items), 138.935458 / c->eps_r,
+    k_unsort<<<nb, 256, 0, st>>>(c->N, c->inv, c->fs, f, (red && n_part > 0) ? c->part : nullptr, n_part,
+                                 138.935458 / c->eps_r,
                                  (flags & NB_ENERGY) ? e : nullptr, (flags & NB_VIRIAL) ? vir : nullptr);
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;

@@ -222,7 +222,9 @@ nb_status nb_cuda_status(cudaError_t e);
 nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir);
 // positions of the last force call (sorted mode: the caller's array), else of the last gather or sort
 inline const float4 *nb_cur_xq(const nb_ctx *c) { return c->xq_cur ? c->xq_cur : c->xq; }
-int nb_force_blocks(int n_items);
+// upper bound on the partial-sum rows of a force launch (one per warp; at most one
+// warp per work item, rounded up to whole blocks of 4 warps)
+inline int nb_force_rows_max(int n_items) { return n_items + 4; }
 
 // launchers (one per translation unit)
 nb_status nb_launch_grid_sort(nb_ctx *c, const float *x, cudaStream_t st);
