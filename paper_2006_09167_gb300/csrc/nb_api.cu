@@ -122,6 +122,8 @@ nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     v.ew_beta2 = (float)(c->beta * c->beta);
     v.ew_beta_lo = (float)(c->beta - (double)v.ew_beta);
     v.ew_beta2_lo = (float)(c->beta * c->beta - (double)v.ew_beta2);
+    v.ew_bt = v.ew_beta * (float)(1.0 / NB_EW_ZMAX_D);
+    v.ew_bt_lo = v.ew_beta_lo * (float)(1.0 / NB_EW_ZMAX_D);
     v.ew_2bsp = (float)(2.0 * c->beta / sqrt(M_PI));
     return v;
 }

@@ -69,6 +69,7 @@ struct SysView {
     float ew_beta2;  // beta^2 (float pair with ew_beta2_lo)
     float ew_beta_lo, ew_beta2_lo;  // beta - (float)beta, beta^2 - (float)beta^2
     float ew_2bsp;   // 2 beta / sqrt(pi)
+    float ew_bt, ew_bt_lo;  // beta / ZMAX as a float pair (X(z) is evaluated in t = z / ZMAX)
     float rc6inv, rc12inv;
     int *queue;  // work-item counter of the persistent force kernel (zeroed by the gather)
     unsigned short *kept;  // first-use prune fused into the force kernel: half masks per outer entry

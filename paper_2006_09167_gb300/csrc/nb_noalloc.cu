@@ -277,6 +277,8 @@ extern "C" nb_status nb_forces_small_noalloc(const nb_params *p, const float *x_
     a.v.ew_beta2 = (float)(p->beta * p->beta);
     a.v.ew_beta_lo = (float)(p->beta - (double)a.v.ew_beta);
     a.v.ew_beta2_lo = (float)(p->beta * p->beta - (double)a.v.ew_beta2);
+    a.v.ew_bt = a.v.ew_beta * (float)(1.0 / NB_EW_ZMAX_D);
+    a.v.ew_bt_lo = a.v.ew_beta_lo * (float)(1.0 / NB_EW_ZMAX_D);
     a.v.ew_2bsp = (float)(2.0 * p->beta / sqrt(M_PI));
     a.v.rc6inv = (float)rc6inv;
     a.v.rc12inv = (float)(rc6inv * rc6inv);

@@ -10,6 +10,31 @@ namespace nbk {
 static_assert(NB_EW_ZMAX == (float)NB_EW_ZMAX_D, "Ewald fit range");
 
 
+// Hardware approximations in their flush-to-zero forms.  Without .ftz the
+// compiler wraps each one in a rescaling for denormal inputs (a compare, two
+// multiplies and a select); no input here is denormal (squared distances are
+// clamped to at most rc^2 and at least the closest pair's, denominators of the
+// rationals are >= 1), so the results are the same and the wrapper is dead code
+// that cost 9% of the force kernel's instructions.
+__device__ __forceinline__ float rsq_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float div_approx(float a, float b) {
+    float r;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+
 __device__ __forceinline__ float ew_h(float s) {
     float p = fmaf(NB_EW_HP6, s, NB_EW_HP5);
     p = fmaf(p, s, NB_EW_HP4);
@@ -22,15 +47,21 @@ __device__ __forceinline__ float ew_h(float s) {
     q = fmaf(q, s, NB_EW_HQ2);
     q = fmaf(q, s, NB_EW_HQ1);
     q = fmaf(q, s, 1.0f);
-    return __fdividef(p, q);
+    return div_approx(p, q);
 }
 
 // exp(-x) for 0 <= x < 80: x = n ln2 + u (Cody-Waite reduction; n * LN2_HI is
 // exact), exp(-u) by the degree-7 polynomial 1 + w q(w) with w = -u, times 2^-n
+//
+// n = rint(x log2 e) by the 1.5 * 2^23 shift: m = x log2 e + 1.5 * 2^23 rounds to an
+// integer whose low mantissa bits hold n (0 <= n < 2^22), -n = 1.5 * 2^23 - m is exact,
+// and the scale 2^-n has the bits 0x3f800000 - (bits(m) << 23).  Same n as rintf
+// (round half to even) without the float -> int conversions.
 __device__ __forceinline__ float ew_expm(float x) {
-    const float n = rintf(x * NB_EXP_LOG2E);
-    float u = fmaf(-n, NB_EXP_LN2_HI, x);
-    u = fmaf(-n, NB_EXP_LN2_LO, u);
+    const float m = __fadd_rn(__fmul_rn(x, NB_EXP_LOG2E), 12582912.0f);
+    const float nn = __fsub_rn(12582912.0f, m);
+    float u = fmaf(nn, NB_EXP_LN2_HI, x);
+    u = fmaf(nn, NB_EXP_LN2_LO, u);
     const float w = -u;
     float q = fmaf(NB_EXP_C7, w, NB_EXP_C6);
     q = fmaf(q, w, NB_EXP_C5);
@@ -39,7 +70,7 @@ __device__ __forceinline__ float ew_expm(float x) {
     q = fmaf(q, w, NB_EXP_C2);
     q = fmaf(q, w, NB_EXP_C1);
     const float p = fmaf(q, w, 1.0f);
-    return p * __int_as_float((127 - (int)n) << 23);
+    return p * __int_as_float(0x3f800000 - (__float_as_int(m) << 23));
 }
 
 // Reciprocal of q > 0 within about half an ulp: the hardware approximation
@@ -48,13 +79,12 @@ __device__ __forceinline__ float ew_expm(float x) {
 // that varies with z, and the Coulomb energy of water -- a sum whose terms cancel
 // about 3000-fold -- turned that into a relative energy error of 2e-6.
 __device__ __forceinline__ float rcp_refined(float q) {
-    const float r = __fdividef(1.0f, q);
+    const float r = rcp_approx(q);
     return fmaf(r, fmaf(-q, r, 1.0f), r);
 }
 
-// X(z) = exp(z^2) erfc(z), a (6,6) rational in t = z / ZMAX
-__device__ __forceinline__ float ew_x(float z) {
-    const float t = z * (1.0f / NB_EW_ZMAX);
+// X(z) = exp(z^2) erfc(z), a (6,6) rational in t = z / ZMAX (the argument)
+__device__ __forceinline__ float ew_x(float t) {
     float p = fmaf(NB_EW_XP6, t, NB_EW_XP5);
     p = fmaf(p, t, NB_EW_XP4);
     p = fmaf(p, t, NB_EW_XP3);
@@ -94,14 +124,15 @@ __device__ __forceinline__ float2 ew_h2(float2 s) {
     q = pfma(q, s, p2(NB_EW_HQ2));
     q = pfma(q, s, p2(NB_EW_HQ1));
     q = pfma(q, s, p2(1.0f));
-    return make_float2(__fdividef(p.x, q.x), __fdividef(p.y, q.y));
+    return make_float2(div_approx(p.x, q.x), div_approx(p.y, q.y));
 }
 
 __device__ __forceinline__ float2 ew_expm2(float2 x) {
     const float2 nl = pmul(x, p2(NB_EXP_LOG2E));
-    const float2 n = make_float2(rintf(nl.x), rintf(nl.y));
-    float2 u = pfma(pneg(n), p2(NB_EXP_LN2_HI), x);
-    u = pfma(pneg(n), p2(NB_EXP_LN2_LO), u);
+    const float2 m = padd(nl, p2(12582912.0f));
+    const float2 nn = psub(p2(12582912.0f), m);  // -n, exact
+    float2 u = pfma(nn, p2(NB_EXP_LN2_HI), x);
+    u = pfma(nn, p2(NB_EXP_LN2_LO), u);
     const float2 w = pneg(u);
     float2 q = pfma(p2(NB_EXP_C7), w, p2(NB_EXP_C6));
     q = pfma(q, w, p2(NB_EXP_C5));
@@ -110,11 +141,11 @@ __device__ __forceinline__ float2 ew_expm2(float2 x) {
     q = pfma(q, w, p2(NB_EXP_C2));
     q = pfma(q, w, p2(NB_EXP_C1));
     const float2 p = pfma(q, w, p2(1.0f));
-    return pmul(p, make_float2(__int_as_float((127 - (int)n.x) << 23), __int_as_float((127 - (int)n.y) << 23)));
+    return pmul(p, make_float2(__int_as_float(0x3f800000 - (__float_as_int(m.x) << 23)),
+                               __int_as_float(0x3f800000 - (__float_as_int(m.y) << 23))));
 }
 
-__device__ __forceinline__ float2 ew_x2(float2 z) {
-    const float2 t = pmul(z, p2(1.0f / NB_EW_ZMAX));
+__device__ __forceinline__ float2 ew_x2(float2 t) {
     float2 p = pfma(p2(NB_EW_XP6), t, p2(NB_EW_XP5));
     p = pfma(p, t, p2(NB_EW_XP4));
     p = pfma(p, t, p2(NB_EW_XP3));
@@ -127,7 +158,7 @@ __device__ __forceinline__ float2 ew_x2(float2 z) {
     q = pfma(q, t, p2(NB_EW_XQ2));
     q = pfma(q, t, p2(NB_EW_XQ1));
     q = pfma(q, t, p2(1.0f));
-    float2 r = make_float2(__fdividef(1.0f, q.x), __fdividef(1.0f, q.y));  // rcp_refined per component
+    float2 r = make_float2(rcp_approx(q.x), rcp_approx(q.y));  // rcp_refined per component
     r = pfma(r, pfma(pneg(q), r, p2(1.0f)), r);
     return pmul(p, r);
 }
@@ -206,7 +237,7 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
     float r2 = fmaf(d.z, d.z, fmaf(d.y, d.y, d.x * d.x));
     const bool in = bit && (r2 < v.rc2);
     r2 = in ? r2 : v.rc2;
-    float rinv = rsqrtf(r2);
+    float rinv = rsq_approx(r2);
     if (EN) rinv = rsqrt_refine(r2, rinv);
     const float rinv2 = rinv * rinv;
     const float rinv6 = rinv2 * rinv2 * rinv2;
@@ -219,12 +250,13 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
     } else if (COUL == NB_COULOMB_EWALD) {
         if (EN) {
             // one exp(-z^2) serves the energy, erfc(z) = exp(-z^2) X(z), and the force;
-            // z = beta r and z^2 = beta^2 r^2 take beta and beta^2 as float pairs, so
-            // their FP32 rounding leaves no error that grows with z (each pair of the
-            // energy sum then carries only unbiased roundings)
+            // t = z / ZMAX = (beta / ZMAX) r and z^2 = beta^2 r^2 take beta / ZMAX and
+            // beta^2 as float pairs, so their FP32 rounding leaves no error that grows
+            // with z (each pair of the energy sum then carries only unbiased roundings;
+            // ZMAX is a power of two, so t is z / ZMAX exactly)
             const float r = r2 * rinv;
             const float ex = ew_expm(fmaf(r2, v.ew_beta2, r2 * v.ew_beta2_lo));
-            erfcz = ex * ew_x(fmaf(v.ew_beta, r, v.ew_beta_lo * r));
+            erfcz = ex * ew_x(fmaf(v.ew_bt, r, v.ew_bt_lo * r));
             fc = qq * rinv2 * fmaf(erfcz, rinv, v.ew_2bsp * ex);
         } else {
             fc = qq * fmaf(rinv, rinv2, -v.ew_beta3 * ew_h(r2 * v.ew_s));
@@ -265,7 +297,7 @@ __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__re
     const bool in0 = b0 && (r2.x < v.rc2), in1 = b1 && (r2.y < v.rc2);
     r2.x = in0 ? r2.x : v.rc2;
     r2.y = in1 ? r2.y : v.rc2;
-    float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    float2 rinv = make_float2(rsq_approx(r2.x), rsq_approx(r2.y));
     if (EN) {  // rsqrt_refine
         const float2 e = pfma(pneg(pmul(r2, rinv)), rinv, p2(1.0f));
         rinv = pfma(pmul(p2(0.5f), rinv), e, rinv);
@@ -282,7 +314,7 @@ __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__re
         if (EN) {
             const float2 r = pmul(r2, rinv);
             const float2 ex = ew_expm2(pfma(r2, p2(v.ew_beta2), pmul(r2, p2(v.ew_beta2_lo))));
-            erfcz = pmul(ex, ew_x2(pfma(p2(v.ew_beta), r, pmul(p2(v.ew_beta_lo), r))));
+            erfcz = pmul(ex, ew_x2(pfma(p2(v.ew_bt), r, pmul(p2(v.ew_bt_lo), r))));
             fc = pmul(pmul(qq, rinv2), pfma(erfcz, rinv, pmul(p2(v.ew_2bsp), ex)));
         } else {
             fc = pmul(qq, pfma(rinv, rinv2, pmul(p2(-v.ew_beta3), ew_h2(pmul(r2, p2(v.ew_s))))));
@@ -379,15 +411,16 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             const int k = __ffs(both) - 1;
             both &= both - 1;
             const bool b0 = (mw >> (2 * k)) & 1u, b1 = (mw >> (2 * k + 1)) & 1u;
-            const float4 xi = s_xi[k * NB_CL + ti];
             const int tio = s_ti[k * NB_CL + ti];
+            const float4 xi = s_xi[k * NB_CL + ti];
             const float2 dx = psub(p2(xi.x), jx), dy = psub(p2(xi.y), jy), dz = psub(p2(xi.z), jz);
+            const float2 qi2 = p2(xi.w);
             if (PRUNE) {  // same distances, same rounding as the separate prune pass
                 const float2 r2 = pfma(dz, dz, pfma(dy, dy, pmul(dx, dx)));
                 keep_lo |= (int)__any_sync(full, r2.x < v.rin2) << k;
                 keep_hi |= (int)__any_sync(full, r2.y < v.rin2) << k;
             }
-            const float2 p = pair_phi2<COUL, EN>(v, ljt, lje, dx, dy, dz, p2(xi.w), jq, tio + tj0, tio + tj1, b0,
+            const float2 p = pair_phi2<COUL, EN>(v, ljt, lje, dx, dy, dz, qi2, jq, tio + tj0, tio + tj1, b0,
                                                  b1, elj2, ec2);
             const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
             float *fk = s_fi + k * 96 + lane;

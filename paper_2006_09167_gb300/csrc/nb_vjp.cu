@@ -60,7 +60,7 @@ __device__ __forceinline__ bool vjp_pair(const VjpView &v, const float4 *__restr
     float r2 = fmaf(d.z, d.z, fmaf(d.y, d.y, d.x * d.x));
     const bool in = bit && (r2 < sv.rc2);
     r2 = in ? r2 : sv.rc2;
-    float rinv = rsqrtf(r2);
+    float rinv = rsq_approx(r2);
     rinv = rsqrt_refine(r2, rinv);
     const float rinv2 = rinv * rinv;
     const float rinv6 = rinv2 * rinv2 * rinv2;
@@ -81,7 +81,7 @@ __device__ __forceinline__ bool vjp_pair(const VjpView &v, const float4 *__restr
         const float r = r2 * rinv;
         const float z = sv.ew_beta * r;
         const float ez = __expf(-z * z);
-        const float ec = ez * ew_x(z);
+        const float ec = ez * ew_x(z * (1.0f / NB_EW_ZMAX));
         const float ex = v.two_beta_sqrtpi * ez;
         psi = f * fmaf(ec, rinv, ex) * rinv2;
         dpsi = f * (-3.f * ec * rinv2 * rinv2 * rinv - ex * fmaf(3.f, rinv2 * rinv2, 2.f * sv.ew_beta * sv.ew_beta * rinv2));

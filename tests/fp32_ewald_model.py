@@ -2,7 +2,9 @@
 
 The energy kernels form, per pair and in FP32 (every FMA rounded once):
     d = x_i - x_j,  r2 = d.d,  1/r (hardware estimate refined by one Newton step),
-    r = r2 / r,  z = beta r  and  x = beta^2 r2  (beta, beta^2 as float pairs),
+    r = r2 / r,  z = beta r  and  x = beta^2 r2  (beta, beta^2 as float pairs; the
+    kernels form t = z / ZMAX directly from beta / ZMAX, the same value because ZMAX
+    is a power of two),
     exp(-x) by Cody-Waite reduction and a degree-7 polynomial,
     X(z) = exp(z^2) erfc(z) as a (6,6) rational with a refined reciprocal,
     erfc(z) = exp(-x) X(z),  v = erfc(z) / r - erfc(beta rc) / rc,  term = qi qj v.
