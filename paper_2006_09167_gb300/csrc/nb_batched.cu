@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(kBW * 32)
             float vr[9];
 #pragma unroll
             for (int k = 0; k < 9; k++) vr[k] = 0.f;
-            process_item<COUL, EN, VIR>(v, m.y, nj, v.lj, v.lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
+            const LjTables ljt = {v.lj, v.lje, nullptr, nullptr, nullptr};
+            process_item<COUL, EN, VIR>(v, m.y, nj, ljt, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
             __syncwarp();
             if (EN || VIR) {
                 warp_reduce_outputs<EN, VIR>(elj, ec, vr);

@@ -30,23 +30,49 @@ using namespace nbk;
 namespace {
 
 constexpr int kFW = 4;  // warps (work items) per block
+constexpr int kLj3MaxT = 8;  // largest type count with the T^3 parameter table (48 B x 512 = 24 KB)
+
+// dynamic shared memory of the force kernel: the T x T tables, and for LJ3 the T^3 ones
+__host__ __device__ inline size_t forces_smem(int T, bool en, bool lj3) {
+    const size_t t2 = (size_t)T * T, t3 = lj3 ? t2 * T : 0;
+    return t2 * (sizeof(float2) + (en ? sizeof(float4) : 0)) + t3 * (sizeof(float4) + (en ? sizeof(float4) + sizeof(float2) : 0));
+}
 
 // Persistent: a grid sized to the resident capacity of the GPU, each warp taking
 // the next work item (ordered longest first) from a device counter, so the
 // kernel tail is at most one item long (paper Sec. V.F: tails from uneven work).
-template <int COUL, bool EN, bool VIR, bool PRUNE = false>
+template <int COUL, bool EN, bool VIR, bool PRUNE = false, bool LJ3 = false>
 __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
     extern __shared__ float4 s_dyn[];
-    float4 *s_lje = s_dyn;                                                  // EN only: [T*T]
-    float2 *s_lj = reinterpret_cast<float2 *>(s_dyn + (EN ? v.T * v.T : 0));  // [T*T]
+    const int T = v.T, T2 = T * T, T3 = LJ3 ? T2 * T : 0;
+    // float4 arrays first: lje [T2] (EN), l3f [T3], l3e [T3] (EN); then float2: lj [T2], l3s [T3] (EN)
+    float4 *s_lje = s_dyn;
+    float4 *s_l3f = s_lje + (EN ? T2 : 0);
+    float4 *s_l3e = s_l3f + T3;
+    float2 *s_lj = reinterpret_cast<float2 *>(s_l3e + (EN ? T3 : 0));
+    float2 *s_l3s = s_lj + T2;
     __shared__ float4 s_xi[kFW][NB_SCA];
     __shared__ int s_ti[kFW][NB_SCA];
     __shared__ float s_fi[kFW][3 * NB_SCL * 32];
-    for (int t = threadIdx.x; t < v.T * v.T; t += blockDim.x) {
+    for (int t = threadIdx.x; t < T2; t += blockDim.x) {
         s_lj[t] = v.lj[t];
         if (EN) s_lje[t] = v.lje[t];
     }
+    if (LJ3) {
+        // entry (a, b0, b1): the parameters of pairs (a, b0) and (a, b1), component-wise
+        for (int t = threadIdx.x; t < T3; t += blockDim.x) {
+            const int a = t / T2, b0 = (t / T) % T, b1 = t % T;
+            const float2 f0 = v.lj[a * T + b0], f1 = v.lj[a * T + b1];
+            s_l3f[t] = make_float4(f0.x, f1.x, f0.y, f1.y);
+            if (EN) {
+                const float4 e0 = v.lje[a * T + b0], e1 = v.lje[a * T + b1];
+                s_l3e[t] = make_float4(e0.x, e1.x, e0.y, e1.y);
+                s_l3s[t] = make_float2(e0.z, e1.z);
+            }
+        }
+    }
     __syncthreads();
+    const LjTables ljt = {s_lj, s_lje, s_l3f, s_l3e, s_l3s};
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
     // first item: the warp's index in the grid; later items from the counter,
@@ -61,7 +87,7 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
 #pragma unroll
         for (int k = 0; k < 9; k++) vr[k] = 0.f;
         if (nj > 0)
-            process_item<COUL, EN, VIR, PRUNE>(v, w, nj, s_lj, s_lje, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
+            process_item<COUL, EN, VIR, PRUNE, LJ3>(v, w, nj, ljt, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
         if (EN || VIR) {
             // FP32 warp reduction of the item's sums, added in FP64 to the warp's row
             warp_reduce_outputs<EN, VIR>(elj, ec, vr);
@@ -185,21 +211,28 @@ __global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__res
 }
 
 // Returns the number of partial-sum rows the launch writes (one per warp).
-template <int COUL, bool EN, bool VIR, bool PRUNE = false>
+template <int COUL, bool EN, bool VIR, bool PRUNE = false, bool LJ3 = false>
 int launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
-    const size_t smem = (sizeof(float2) + (EN ? sizeof(float4) : 0)) * v.T * v.T;
+    const size_t smem = forces_smem(v.T, EN, LJ3);
     // the type-pair tables of many types, with the 17 KB of static staging arrays,
     // exceed the default 48 KB of shared memory (64 types: 96 KB of tables); opt in
     // to the larger carve-out, at lower occupancy
     if (smem > 16 * 1024)
-        cudaFuncSetAttribute(k_forces<COUL, EN, VIR, PRUNE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_forces<COUL, EN, VIR, PRUNE, LJ3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_forces<COUL, EN, VIR, PRUNE>, kFW * 32, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_forces<COUL, EN, VIR, PRUNE, LJ3>, kFW * 32, smem) != cudaSuccess ||
         occ < 1)
         occ = 1;
     const int blocks = std::min((v.n_items + kFW - 1) / kFW, std::max(n_sm, 1) * occ);
-    k_forces<COUL, EN, VIR, PRUNE><<<blocks, kFW * 32, smem, st>>>(v);
+    k_forces<COUL, EN, VIR, PRUNE, LJ3><<<blocks, kFW * 32, smem, st>>>(v);
     return blocks * kFW;
+}
+
+// the T^3 parameter table where it fits (few types), the T x T tables otherwise
+template <int COUL, bool EN, bool VIR>
+int launch_pick(const SysView &v, int n_sm, cudaStream_t st) {
+    return v.T <= kLj3MaxT ? launch_forces_t<COUL, EN, VIR, false, true>(v, n_sm, st)
+                           : launch_forces_t<COUL, EN, VIR, false, false>(v, n_sm, st);
 }
 
 }  // namespace
@@ -241,20 +274,20 @@ nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cu
 int nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, int n_sm, cudaStream_t st) {
     const bool en = flags & NB_ENERGY, vi = flags & NB_VIRIAL;
     if (coulomb == NB_COULOMB_RF) {
-        if (en && vi) return launch_forces_t<NB_COULOMB_RF, true, true>(v, n_sm, st);
-        else if (en) return launch_forces_t<NB_COULOMB_RF, true, false>(v, n_sm, st);
-        else if (vi) return launch_forces_t<NB_COULOMB_RF, false, true>(v, n_sm, st);
-        else return launch_forces_t<NB_COULOMB_RF, false, false>(v, n_sm, st);
+        if (en && vi) return launch_pick<NB_COULOMB_RF, true, true>(v, n_sm, st);
+        else if (en) return launch_pick<NB_COULOMB_RF, true, false>(v, n_sm, st);
+        else if (vi) return launch_pick<NB_COULOMB_RF, false, true>(v, n_sm, st);
+        else return launch_pick<NB_COULOMB_RF, false, false>(v, n_sm, st);
     } else if (coulomb == NB_COULOMB_EWALD) {
-        if (en && vi) return launch_forces_t<NB_COULOMB_EWALD, true, true>(v, n_sm, st);
-        else if (en) return launch_forces_t<NB_COULOMB_EWALD, true, false>(v, n_sm, st);
-        else if (vi) return launch_forces_t<NB_COULOMB_EWALD, false, true>(v, n_sm, st);
-        else return launch_forces_t<NB_COULOMB_EWALD, false, false>(v, n_sm, st);
+        if (en && vi) return launch_pick<NB_COULOMB_EWALD, true, true>(v, n_sm, st);
+        else if (en) return launch_pick<NB_COULOMB_EWALD, true, false>(v, n_sm, st);
+        else if (vi) return launch_pick<NB_COULOMB_EWALD, false, true>(v, n_sm, st);
+        else return launch_pick<NB_COULOMB_EWALD, false, false>(v, n_sm, st);
     } else {
-        if (en && vi) return launch_forces_t<NB_COULOMB_NONE, true, true>(v, n_sm, st);
-        else if (en) return launch_forces_t<NB_COULOMB_NONE, true, false>(v, n_sm, st);
-        else if (vi) return launch_forces_t<NB_COULOMB_NONE, false, true>(v, n_sm, st);
-        else return launch_forces_t<NB_COULOMB_NONE, false, false>(v, n_sm, st);
+        if (en && vi) return launch_pick<NB_COULOMB_NONE, true, true>(v, n_sm, st);
+        else if (en) return launch_pick<NB_COULOMB_NONE, true, false>(v, n_sm, st);
+        else if (vi) return launch_pick<NB_COULOMB_NONE, false, true>(v, n_sm, st);
+        else return launch_pick<NB_COULOMB_NONE, false, false>(v, n_sm, st);
     }
 }
 

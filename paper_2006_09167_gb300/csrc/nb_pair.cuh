@@ -286,13 +286,59 @@ __device__ __forceinline__ float pair_phi(const SysView &v, const float2 *__rest
     return phi;
 }
 
+// Lennard-Jones parameters of the two pairs of a packed iteration, one component
+// per pair: 6 C6, 12 C12 (forces) and C6, C12, C12/rc^12 - C6/rc^6 (energies).
+struct Lj2 {
+    float2 f6, f12, e6, e12, sh;
+};
+
+// The type-pair tables (T x T) and, for few types, the same values rearranged by
+// (i-type, j-type of the lower j-atom, j-type of the upper j-atom), T^3 entries, so
+// that one load yields both pairs' parameters already packed.
+struct LjTables {
+    const float2 *lj;   // [T*T] (6 C6, 12 C12)
+    const float4 *lje;  // [T*T] (C6, C12, C12/rc^12 - C6/rc^6, 0)
+    const float4 *l3f;  // [T^3] (6 C6, 6 C6', 12 C12, 12 C12')
+    const float4 *l3e;  // [T^3] (C6, C6', C12, C12')
+    const float2 *l3s;  // [T^3] (shift, shift')
+};
+
+template <bool EN>
+__device__ __forceinline__ Lj2 lj_gather(const LjTables &t, int tp0, int tp1) {
+    Lj2 r;
+    const float2 la = t.lj[tp0], lb = t.lj[tp1];
+    r.f6 = make_float2(la.x, lb.x);
+    r.f12 = make_float2(la.y, lb.y);
+    if (EN) {
+        const float4 ea = t.lje[tp0], eb = t.lje[tp1];
+        r.e6 = make_float2(ea.x, eb.x);
+        r.e12 = make_float2(ea.y, eb.y);
+        r.sh = make_float2(ea.z, eb.z);
+    }
+    return r;
+}
+
+template <bool EN>
+__device__ __forceinline__ Lj2 lj_triple(const LjTables &t, int idx) {
+    Lj2 r;
+    const float4 f = t.l3f[idx];
+    r.f6 = make_float2(f.x, f.y);
+    r.f12 = make_float2(f.z, f.w);
+    if (EN) {
+        const float4 e = t.l3e[idx];
+        r.e6 = make_float2(e.x, e.y);
+        r.e12 = make_float2(e.z, e.w);
+        r.sh = t.l3s[idx];
+    }
+    return r;
+}
+
 // Two pairs at once: pair_phi's operations, in the same order, on float2 values
 // (component 0: the first pair, component 1: the second; i-charges qi and
 // j-charges qj per component).  Energies are added per component to elj / ec.
 template <int COUL, bool EN>
-__device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__restrict__ ljt,
-                                            const float4 *__restrict__ lje, float2 dx, float2 dy, float2 dz, float2 qi,
-                                            float2 qj, int tp0, int tp1, bool b0, bool b1, float2 &elj, float2 &ec) {
+__device__ __forceinline__ float2 pair_phi2(const SysView &v, const Lj2 &lj, float2 dx, float2 dy, float2 dz, float2 qi,
+                                            float2 qj, bool b0, bool b1, float2 &elj, float2 &ec) {
     float2 r2 = pfma(dz, dz, pfma(dy, dy, pmul(dx, dx)));
     const bool in0 = b0 && (r2.x < v.rc2), in1 = b1 && (r2.y < v.rc2);
     r2.x = in0 ? r2.x : v.rc2;
@@ -304,8 +350,7 @@ __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__re
     }
     const float2 rinv2 = pmul(rinv, rinv);
     const float2 rinv6 = pmul(pmul(rinv2, rinv2), rinv2);
-    const float2 la = ljt[tp0], lb = ljt[tp1];  // (6 C6, 12 C12)
-    const float2 flj = pmul(rinv6, pfma(make_float2(la.y, lb.y), rinv6, make_float2(-la.x, -lb.x)));
+    const float2 flj = pmul(rinv6, pfma(lj.f12, rinv6, pneg(lj.f6)));
     const float2 qq = pmul(qi, qj);
     float2 fc = p2(0.f), erfcz = p2(0.f);
     if (COUL == NB_COULOMB_RF) {
@@ -325,9 +370,7 @@ __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__re
     phi.x = in0 ? phi.x : 0.f;
     phi.y = in1 ? phi.y : 0.f;
     if (EN) {
-        const float4 ea = lje[tp0], eb = lje[tp1];  // (C6, C12, C12/rc^12 - C6/rc^6, -)
-        float2 vlj = pfma(rinv6, pfma(make_float2(ea.y, eb.y), rinv6, make_float2(-ea.x, -eb.x)),
-                          make_float2(-ea.z, -eb.z));
+        float2 vlj = pfma(rinv6, pfma(lj.e12, rinv6, pneg(lj.e6)), pneg(lj.sh));
         float2 vc = p2(0.f);
         if (COUL == NB_COULOMB_RF) {
             const float2 t_hi = pmul(rinv, rinv);
@@ -351,8 +394,9 @@ __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__re
 
 // Evaluate work item w (nj > 0 inner entries) with one warp.  s_xi / s_ti are
 // this warp's 64-entry staging arrays and s_fi its i-force accumulators
-// ([8 clusters][3][32 lanes] floats, conflict-free); ljt / lje the pair tables
-// (shared or global memory).  Forces are added to v.f; energies and the virial
+// ([8 clusters][3][32 lanes] floats, conflict-free); ljt the type-pair tables
+// (shared or global memory; LJ3: the i-clusters that interact with both j-halves
+// read the rearranged T^3 table, one load for both pairs).  Forces are added to v.f; energies and the virial
 // sum of r (x) F go to the caller's per-lane accumulators.  The i-cluster loop
 // walks the set bits of the interaction mask (a warp-uniform loop) and is not
 // unrolled, so the kernel stays small enough for the instruction cache and the
@@ -362,8 +406,8 @@ __device__ __forceinline__ float2 pair_phi2(const SysView &v, const float2 *__re
 // (one 8-bit mask for both j-halves); while computing the forces the warp also
 // records, per i-cluster and j-half, whether any atom pair is closer than r_in,
 // and writes those half masks to v.kept for the compaction into the inner list.
-template <int COUL, bool EN, bool VIR, bool PRUNE = false>
-__device__ __forceinline__ void process_item(const SysView &v, int w, int nj, const float2 *ljt, const float4 *lje,
+template <int COUL, bool EN, bool VIR, bool PRUNE = false, bool LJ3 = false>
+__device__ __forceinline__ void process_item(const SysView &v, int w, int nj, const LjTables &ljt,
                                              float4 *s_xi, int *s_ti, float *s_fi, KSum &elj, KSum &ec,
                                              float (&vr)[9]) {
     const int lane = threadIdx.x & 31;
@@ -396,6 +440,7 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             xj1 = shift_j(xj1, sh);
         }
         const int tj0 = v.type[cj * NB_CL + tj], tj1 = v.type[cj * NB_CL + tj + 4];
+        const int tjj = LJ3 ? tj0 * v.T + tj1 : 0;  // (j-type, j-type') row of the T^3 table
         // exclusion bits of the lane's two pairs for every i-cluster k (bits 2k, 2k + 1)
         const unsigned mw = mg ? (unsigned)v.mask_lanes[(size_t)(mg - 1) * 32 + lane] : 0xffffu;
         // the lane's two j-atoms as packed pairs (component 0: tj, component 1: tj + 4)
@@ -420,8 +465,8 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
                 keep_lo |= (int)__any_sync(full, r2.x < v.rin2) << k;
                 keep_hi |= (int)__any_sync(full, r2.y < v.rin2) << k;
             }
-            const float2 p = pair_phi2<COUL, EN>(v, ljt, lje, dx, dy, dz, qi2, jq, tio + tj0, tio + tj1, b0,
-                                                 b1, elj2, ec2);
+            const Lj2 lj = LJ3 ? lj_triple<EN>(ljt, tio * v.T + tjj) : lj_gather<EN>(ljt, tio + tj0, tio + tj1);
+            const float2 p = pair_phi2<COUL, EN>(v, lj, dx, dy, dz, qi2, jq, b0, b1, elj2, ec2);
             const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
             float *fk = s_fi + k * 96 + lane;
             fk[0] += ax.x + ax.y;
@@ -447,9 +492,10 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             const float2 dx = psub(make_float2(xia.x, xib.x), make_float2(xja.x, xjb.x));
             const float2 dy = psub(make_float2(xia.y, xib.y), make_float2(xja.y, xjb.y));
             const float2 dz = psub(make_float2(xia.z, xib.z), make_float2(xja.z, xjb.z));
-            const float2 p = pair_phi2<COUL, EN>(v, ljt, lje, dx, dy, dz, make_float2(xia.w, xib.w),
-                                                 make_float2(xja.w, xjb.w), s_ti[ka * NB_CL + ti] + (ua ? tj1 : tj0),
-                                                 s_ti[kb * NB_CL + ti] + (ub ? tj1 : tj0), ba, bb, elj2, ec2);
+            const Lj2 lj = lj_gather<EN>(ljt, s_ti[ka * NB_CL + ti] + (ua ? tj1 : tj0),
+                                         s_ti[kb * NB_CL + ti] + (ub ? tj1 : tj0));
+            const float2 p = pair_phi2<COUL, EN>(v, lj, dx, dy, dz, make_float2(xia.w, xib.w),
+                                                 make_float2(xja.w, xjb.w), ba, bb, elj2, ec2);
             const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
             float *fa = s_fi + ka * 96 + lane;
             float *fb = s_fi + kb * 96 + lane;
@@ -486,7 +532,8 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             const float4 xi = s_xi[k * NB_CL + ti];
             const int tio = s_ti[k * NB_CL + ti];
             const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
-            const float p = pair_phi<COUL, EN>(v, ljt, lje, d, xi.w, xj.w, tio + (upper ? tj1 : tj0), b, elj_e, ec_e);
+            const float p = pair_phi<COUL, EN>(v, ljt.lj, ljt.lje, d, xi.w, xj.w, tio + (upper ? tj1 : tj0), b, elj_e,
+                                               ec_e);
             const float ax = p * d.x, ay = p * d.y, az = p * d.z;
             float *fk = s_fi + k * 96 + lane;
             fk[0] += ax;
