@@ -62,11 +62,12 @@ FLOPS_PER_PAIR_ROOFLINE = {"ewald": 53, "rf": 41, "none": 33}
 # DRAM bytes (read + write) of one k_forces<Ewald, energy, virial> launch on the
 # 96k box, from the committed ncu summary of that kernel (the capture named in
 # FORCE_KERNEL_CAPTURE); None whenever the force kernel has changed since it was taken.
-FORCE_KERNEL_DRAM_BYTES = None
+FORCE_KERNEL_DRAM_BYTES = 7_755_776
 # From the same capture: FP32 (FMA) pipe and issue-slot utilisation of that launch,
 # in percent of active cycles (what bounds the kernel; None with the bytes above).
-FORCE_KERNEL_NCU_PCT = None
-FORCE_KERNEL_CAPTURE = None
+FORCE_KERNEL_NCU_PCT = {"fma_pipe": 57.6, "issue_slots": 70.6}
+FORCE_KERNEL_CAPTURE = ("profiles/k_forces_spce_water_96k.md, mid-life launch of "
+                        "'bench.py --profile --profile-case step', last column (cold L2, one launch)")
 
 
 def rank_env():
@@ -290,6 +291,9 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     launches = ctx.nb_get_stats()["n_launches"] - launches0
+    # algorithmic work of one force launch: the pairs of the list the timed launches used, at the
+    # positions of the end of the timed steps (the clock window below moves the atoms further)
+    n_eff, n_raw = ctx.nb_count_pairs()
     # clock window: the timed region is a few ms, shorter than the sampling interval, so the
     # same steps keep running (untimed, L2 flushed alike) for a further second of sampling
     ctx.nb_trace_enable(False)
@@ -308,8 +312,6 @@ def run_ours(args, rank, world, local_rank):
     total_ms = sum(step_ms)
     fk_ms, fk_n = ctx.nb_trace_read(api.NB_TRACE_FORCES)
     assert ctx.nb_get_error() == 0, "device error during the timed loop"
-    # algorithmic work of one force launch: effective pairs at the current positions
-    n_eff, n_raw = ctx.nb_count_pairs()
     # gather and prune kernel times (reported, not part of the headline): 50 more steps of
     # the same loop, L2 flushed between them as above
     ctx.nb_trace_enable(True, kinds=[api.NB_TRACE_PRUNE, api.NB_TRACE_GATHER])
