@@ -90,7 +90,6 @@ nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     v.mask_lanes = c->mask_lanes;
     v.lj = c->lj;
     v.lje = c->lje;
-    v.part = c->part;
     v.f = f;
     v.e = e;
     v.vir = vir;
@@ -102,6 +101,7 @@ nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     }
     v.rc2 = (float)(c->rc * c->rc);
     v.coul_f = (float)(138.935458 / c->eps_r);
+    v.coul_f64 = 138.935458 / c->eps_r;
     double rc3 = c->rc * c->rc * c->rc;
     double krf = (!isfinite(c->eps_rf) || c->eps_rf <= 0.0) ? 1.0 / (2.0 * rc3)
                                                             : (c->eps_rf - c->eps_r) / ((2.0 * c->eps_rf + c->eps_r) * rc3);
@@ -265,7 +265,6 @@ void nb_destroy(nb_ctx *c) {
     dfree(c->excl_idx);
     dfree(c->lj);
     dfree(c->lje);
-    dfree(c->part);
     dfree(c->gfs);
     dfree(c->gxs);
     dfree(c->gqs);
@@ -441,12 +440,6 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
         if ((s = dalloc(&c->masks, (size_t)cap * 8)) != NB_OK) return s;
         if ((s = dalloc(&c->mask_lanes, (size_t)cap * 32)) != NB_OK) return s;
         c->masks_cap = cap;
-    }
-    const int nblk = nb_force_rows_max(c->n_items) + 1;
-    if (nblk > c->part_cap) {
-        int cap = nblk + nblk / 8 + 16;
-        if ((s = dalloc(&c->part, (size_t)cap * 11)) != NB_OK) return s;
-        c->part_cap = cap;
     }
     int need_sort = c->split * ((c->n_items + 1023) / 1024 + 1);
     if (need_sort > c->sort_tmp_cap) {

@@ -104,10 +104,25 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
         if (lane == 0) claim = atomicAdd(v.queue, 1);
         w = n_warps + __shfl_sync(full, claim, 0);
     }
-    // one row of 11 partial sums per warp of the grid (zeros for a warp without items),
-    // folded by the unsort kernel: a few thousand rows instead of one per work item, and
-    // no block barrier or same-address atomics in this kernel
-    if ((EN || VIR) && lane < 11) v.part[(size_t)(blockIdx.x * kFW + wib) * 11 + lane] = row;
+    // the block's four rows of partial sums, added in FP64 to the outputs (E_LJ, f E_C,
+    // -1/2 of the virial) by 11 atomics per block of the persistent grid: no separate fold
+    // launch, and the blocks finish at different times, so the atomics hardly contend
+    if (EN || VIR) {
+        __shared__ double s_row[kFW][11];
+        if (lane < 11) s_row[wib][lane] = row;
+        __syncthreads();
+        const int t = threadIdx.x;
+        if (t < 11) {
+            double tot = 0.0;
+#pragma unroll
+            for (int q = 0; q < kFW; q++) tot += s_row[q][t];
+            if (t < 2) {
+                if (v.e) atomicAdd(&v.e[t], t == 0 ? tot : v.coul_f64 * tot);
+            } else if (v.vir) {
+                atomicAdd(&v.vir[t - 2], -0.5 * tot);
+            }
+        }
+    }
 }
 
 // Lines the force kernel will read from memory the gather does not write (inner
@@ -174,12 +189,8 @@ __global__ void k_prep_sorted(int nslots, float4 *__restrict__ f, double *e, dou
     if (s < nslots) f[s] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Forces back to caller order; each block also folds a share of the per-block
-// energy/virial partial sums into the FP64 outputs (E_C gets the Coulomb
-// constant here, the virial its factor -1/2).
-__global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__restrict__ fs, float *__restrict__ f,
-                         const double *__restrict__ part, int n_part, double coul_f, double *e, double *vir) {
-    __shared__ double s_acc[256];
+// Forces back to caller order.
+__global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__restrict__ fs, float *__restrict__ f) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const float4 v = fs[inv[i]];
@@ -187,30 +198,9 @@ __global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__res
         f[3 * i + 1] = v.y;
         f[3 * i + 2] = v.z;
     }
-    if (!part) return;
-    // thread t folds value k = t % 11 of the rows r = blockIdx.x + G (t / 11 + 23 m)
-    const int k = threadIdx.x % 11, lane_row = threadIdx.x / 11;
-    double acc = 0.0;
-    if (threadIdx.x < 253) {
-        for (int r = blockIdx.x + gridDim.x * lane_row; r < n_part; r += gridDim.x * 23)
-            acc += part[(size_t)r * 11 + k];
-    }
-    s_acc[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < 11) {
-        double tot = 0.0;
-        for (int l = 0; l < 23; l++) tot += s_acc[l * 11 + threadIdx.x];
-        if (threadIdx.x == 0) {
-            if (e) atomicAdd(&e[0], tot);
-        } else if (threadIdx.x == 1) {
-            if (e) atomicAdd(&e[1], coul_f * tot);
-        } else if (vir) {
-            atomicAdd(&vir[threadIdx.x - 2], -0.5 * tot);
-        }
-    }
 }
 
-// Returns the number of partial-sum rows the launch writes (one per warp).
+// Returns the number of warps of the launch.
 template <int COUL, bool EN, bool VIR, bool PRUNE = false, bool LJ3 = false>
 int launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
     const size_t smem = forces_smem(v.T, EN, LJ3);
@@ -297,7 +287,6 @@ int nb_dispatch_forces(const SysView &v, int coulomb, unsigned flags, int n_sm, 
 nb_status nb_launch_forces_sorted(nb_ctx *c, unsigned flags, const float4 *xq, float4 *f, double *e, double *vir,
                                   cudaStream_t st) {
     const int ns = c->S_host * NB_SCA;
-    const bool red = flags & (NB_ENERGY | NB_VIRIAL);
     double *ee = (flags & NB_ENERGY) ? e : nullptr, *vv = (flags & NB_VIRIAL) ? vir : nullptr;
     long long most = 0;
     const L2Prefetch pf = list_prefetch(c, &most);
@@ -309,16 +298,10 @@ nb_status nb_launch_forces_sorted(nb_ctx *c, unsigned flags, const float4 *xq, f
         k_prep_sorted<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ns, f, ee, vv, c->queue, pf);
     }
     SysView v = nb_make_view(c, f, ee, vv);
-    int n_part = 0;  // partial-sum rows written by the force kernel
-    if (v.n_items > 0) {
+    if (v.n_items > 0) {  // the force kernel also adds the energies and the virial to e and vir
         NbTraceScope tr(c, NB_TRACE_FORCES, st);
-        n_part = nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
+        nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
         c->n_launches++;
-    }
-    if (red && n_part > 0) {  // fold the rows (no forces to scatter): about one row per thread
-        c->n_launches++;
-        k_unsort<<<std::min(1024, (n_part + 22) / 23), 256, 0, st>>>(0, c->inv, c->fs, nullptr, c->part, n_part,
-                                                                    138.935458 / c->eps_r, ee, vv);
     }
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
@@ -326,32 +309,27 @@ nb_status nb_launch_forces_sorted(nb_ctx *c, unsigned flags, const float4 *xq, f
 
 nb_status nb_launch_forces(nb_ctx *c, unsigned flags, float *f, double *e, double *vir, cudaStream_t st,
                            bool fused_prune) {
-    const bool red = flags & (NB_ENERGY | NB_VIRIAL);
     SysView v = nb_make_view(c, c->fs, (flags & NB_ENERGY) ? e : nullptr, (flags & NB_VIRIAL) ? vir : nullptr);
-    int n_part = 0;  // partial-sum rows written by the force kernel
-    if (v.n_items > 0) {
+    if (v.n_items > 0) {  // the force kernel also adds the energies and the virial to e and vir
         NbTraceScope tr(c, NB_TRACE_FORCES, st);
         if (fused_prune) {
-            // first use of a new list: the outer list, pruned on the way (energy and
-            // virial rows are always formed; they are folded only if requested)
+            // first use of a new list: the outer list, pruned on the way (energies and the
+            // virial are always formed; they are added to e and vir only if requested)
             v.cj = c->cj_outer;
             v.kept = c->kept;
             const float re = (float)c->r_in * (1.0f + 2e-6f);  // as the separate prune pass
             v.rin2 = re * re;
-            if (c->coulomb == NB_COULOMB_RF) n_part = launch_forces_t<NB_COULOMB_RF, true, true, true>(v, c->n_sm, st);
-            else if (c->coulomb == NB_COULOMB_EWALD)
-                n_part = launch_forces_t<NB_COULOMB_EWALD, true, true, true>(v, c->n_sm, st);
-            else n_part = launch_forces_t<NB_COULOMB_NONE, true, true, true>(v, c->n_sm, st);
+            if (c->coulomb == NB_COULOMB_RF) launch_forces_t<NB_COULOMB_RF, true, true, true>(v, c->n_sm, st);
+            else if (c->coulomb == NB_COULOMB_EWALD) launch_forces_t<NB_COULOMB_EWALD, true, true, true>(v, c->n_sm, st);
+            else launch_forces_t<NB_COULOMB_NONE, true, true, true>(v, c->n_sm, st);
         } else {
-            n_part = nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
+            nb_dispatch_forces(v, c->coulomb, flags, c->n_sm, st);
         }
         c->n_launches++;
     }
     const int nb = (c->N + 255) / 256;
     c->n_launches++;
-    k_unsort<<<nb, 256, 0, st>>>(c->N, c->inv, c->fs, f, (red && n_part > 0) ? c->part : nullptr, n_part,
-                                 138.935458 / c->eps_r,
-                                 (flags & NB_ENERGY) ? e : nullptr, (flags & NB_VIRIAL) ? vir : nullptr);
+    k_unsort<<<nb, 256, 0, st>>>(c->N, c->inv, c->fs, f);
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
 }

@@ -55,12 +55,12 @@ struct SysView {
     float4 *f;          // sorted force accumulators
     double *e;          // [2] or nullptr
     double *vir;        // [9] or nullptr
-    double *part;       // [blocks*11] per-block energy/virial partial sums
     int n_items;
     int T;
     float box_hi[3], box_lo[3];  // L as float plus the float remainder L - (float)L
     float rc2;
     float coul_f;  // 138.935458 / eps_r
+    double coul_f64;  // the same in FP64 (applied to the Coulomb energy sum)
     float k_rf, c_rf, c_rf_lo;  // c_rf as a float pair (c_rf + c_rf_lo)
     float ew_s;      // beta^2 / ZMAX^2
     float ew_beta3;  // beta^3
@@ -154,11 +154,9 @@ struct nb_ctx {
     float4 *bb = nullptr;   // [S_cap*8*2]
     float4 *sbb = nullptr;  // [S_cap*2]
     float4 *fs = nullptr;   // [S_cap*64]
-    double *part = nullptr; // [part_cap*11] per-block energy/virial partials
     float4 *gfs = nullptr, *gxs = nullptr;  // adjoint: sorted gF, dL/dx  [S_cap*64]
     float *gqs = nullptr;                   // adjoint: sorted dL/dq      [S_cap*64]
     double *gpar = nullptr;                 // adjoint: [2*T*T] parameter gradients
-    int part_cap = 0;
     int S_host = 0;         // exact super-cluster count (read back by the list build)
     // lists
     bool have_list = false;
@@ -223,9 +221,6 @@ nb_status nb_cuda_status(cudaError_t e);
 nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir);
 // positions of the last force call (sorted mode: the caller's array), else of the last gather or sort
 inline const float4 *nb_cur_xq(const nb_ctx *c) { return c->xq_cur ? c->xq_cur : c->xq; }
-// upper bound on the partial-sum rows of a force launch (one per warp; at most one
-// warp per work item, rounded up to whole blocks of 4 warps)
-inline int nb_force_rows_max(int n_items) { return n_items + 4; }
 
 // launchers (one per translation unit)
 nb_status nb_launch_grid_sort(nb_ctx *c, const float *x, cudaStream_t st);

@@ -260,6 +260,7 @@ extern "C" nb_status nb_forces_small_noalloc(const nb_params *p, const float *x_
     const double rc = p->rc, rc3 = rc * rc * rc, rc6inv = 1.0 / (rc3 * rc3);
     a.v.rc2 = (float)(rc * rc);
     a.v.coul_f = (float)(138.935458 / p->eps_r);
+    a.v.coul_f64 = 138.935458 / p->eps_r;
     const double krf = (!isfinite(p->eps_rf) || p->eps_rf <= 0.0)
                            ? 1.0 / (2.0 * rc3)
                            : (p->eps_rf - p->eps_r) / ((2.0 * p->eps_rf + p->eps_r) * rc3);
