@@ -65,6 +65,23 @@ __global__ void k_set_lj(int T, const float *__restrict__ c6, const float *__res
     lj_entry(c6[a * T + b], c6[b * T + a], c12[a * T + b], c12[b * T + a], rc6inv, lj[t], lje[t]);
 }
 
+// entry (a, b0, b1) of the T^3 tables: the parameters of the pairs (a, b0) and (a, b1)
+__host__ __device__ inline void l3_entry(int T, int t, const float2 *lj, const float4 *lje, float4 &f, float4 &e,
+                                         float2 &sh) {
+    const int a = t / (T * T), b0 = (t / T) % T, b1 = t % T;
+    const float2 f0 = lj[a * T + b0], f1 = lj[a * T + b1];
+    const float4 e0 = lje[a * T + b0], e1 = lje[a * T + b1];
+    f = make_float4(f0.x, f1.x, f0.y, f1.y);
+    e = make_float4(e0.x, e1.x, e0.y, e1.y);
+    sh = make_float2(e0.z, e1.z);
+}
+
+__global__ void k_set_l3(int T, const float2 *__restrict__ lj, const float4 *__restrict__ lje, float4 *__restrict__ l3f,
+                         float4 *__restrict__ l3e, float2 *__restrict__ l3s) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T * T * T) l3_entry(T, t, lj, lje, l3f[t], l3e[t], l3s[t]);
+}
+
 __global__ void k_set_q(int n, const float *__restrict__ q, float *__restrict__ qd, const int *__restrict__ perm,
                         int nslots, float *__restrict__ q_s, float4 *__restrict__ xq) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -90,6 +107,9 @@ nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     v.mask_lanes = c->mask_lanes;
     v.lj = c->lj;
     v.lje = c->lje;
+    v.l3f = c->l3f;
+    v.l3e = c->l3e;
+    v.l3s = c->l3s;
     v.f = f;
     v.e = e;
     v.vir = vir;
@@ -222,6 +242,11 @@ nb_status nb_create(const nb_params *p, const float *q_host, const int32_t *type
     NB_TRY_ALLOC(dalloc(&c->excl_idx, excl_n));
     NB_TRY_ALLOC(dalloc(&c->lj, T * T));
     NB_TRY_ALLOC(dalloc(&c->lje, T * T));
+    if (T <= NB_LJ3_MAX_T) {
+        NB_TRY_ALLOC(dalloc(&c->l3f, T * T * T));
+        NB_TRY_ALLOC(dalloc(&c->l3e, T * T * T));
+        NB_TRY_ALLOC(dalloc(&c->l3s, T * T * T));
+    }
     NB_TRY_ALLOC(dalloc(&c->gpar, 2 * T * T));
     NB_TRY_ALLOC(dalloc(&c->counters, 16));
     NB_TRY_ALLOC(dalloc(&c->diag, 4));
@@ -244,6 +269,14 @@ nb_status nb_create(const nb_params *p, const float *q_host, const int32_t *type
         e = cudaMemcpy(c->excl_idx, idx.data(), sizeof(int) * excl_n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->lj, lj.data(), sizeof(float2) * T * T, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->lje, lje.data(), sizeof(float4) * T * T, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && c->l3f) {
+        std::vector<float4> l3f(T * T * T), l3e(T * T * T);
+        std::vector<float2> l3s(T * T * T);
+        for (int t = 0; t < T * T * T; t++) l3_entry(T, t, lj.data(), lje.data(), l3f[t], l3e[t], l3s[t]);
+        e = cudaMemcpy(c->l3f, l3f.data(), sizeof(float4) * T * T * T, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->l3e, l3e.data(), sizeof(float4) * T * T * T, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->l3s, l3s.data(), sizeof(float2) * T * T * T, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->ewald_count, 0, sizeof(unsigned));
     int dev = 0;
@@ -265,6 +298,9 @@ void nb_destroy(nb_ctx *c) {
     dfree(c->excl_idx);
     dfree(c->lj);
     dfree(c->lje);
+    dfree(c->l3f);
+    dfree(c->l3e);
+    dfree(c->l3s);
     dfree(c->gfs);
     dfree(c->gxs);
     dfree(c->gqs);
@@ -326,6 +362,10 @@ nb_status nb_set_lj(nb_ctx *c, const float *c6_dev, const float *c12_dev, void *
     int n = c->T * c->T;
     const double rc6inv = 1.0 / (c->rc * c->rc * c->rc * c->rc * c->rc * c->rc);
     k_set_lj<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(c->T, c6_dev, c12_dev, rc6inv, c->lj, c->lje);
+    if (c->l3f) {
+        const int n3 = n * c->T;
+        k_set_l3<<<(n3 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(c->T, c->lj, c->lje, c->l3f, c->l3e, c->l3s);
+    }
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
 }

@@ -40,7 +40,7 @@ struct BatchRep {
     double coul_f;
 };
 
-template <int COUL, bool EN, bool VIR>
+template <int COUL, bool EN, bool VIR, bool LJ3>
 __global__ void __launch_bounds__(kBW * 32)
     k_forces_batched(const SysView *__restrict__ views, const BatchRep *__restrict__ reps, const int2 *__restrict__ gmap,
                      int total, int *queue, double *e, double *vir) {
@@ -61,8 +61,9 @@ __global__ void __launch_bounds__(kBW * 32)
             float vr[9];
 #pragma unroll
             for (int k = 0; k < 9; k++) vr[k] = 0.f;
-            const LjTables ljt = {v.lj, v.lje, nullptr, nullptr, nullptr};
-            process_item<COUL, EN, VIR>(v, m.y, nj, ljt, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
+            // LJ3: every system has few types; the packed iterations read the T^3 tables
+            const LjTables ljt = {v.lj, v.lje, v.l3f, v.l3e, v.l3s};
+            process_item<COUL, EN, VIR, false, LJ3>(v, m.y, nj, ljt, s_xi[wib], s_ti[wib], s_fi[wib], elj, ec, vr);
             __syncwarp();
             if (EN || VIR) {
                 warp_reduce_outputs<EN, VIR>(elj, ec, vr);
@@ -122,9 +123,10 @@ __global__ void k_batch_unsort(const BatchRep *__restrict__ reps, const int2 *__
 }
 
 template <int COUL, bool EN, bool VIR>
-int occupancy() {
+int occupancy(bool lj3) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forces_batched<COUL, EN, VIR>, kBW * 32, 0);
+    if (lj3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forces_batched<COUL, EN, VIR, true>, kBW * 32, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forces_batched<COUL, EN, VIR, false>, kBW * 32, 0);
     return nb > 0 ? nb : 1;
 }
 
@@ -137,6 +139,7 @@ struct nb_batch {
     int total_items = 0;
     int n_gblk = 0, n_ublk = 0;
     int grid = 0;
+    bool lj3 = true;  // every system keeps the T^3 parameter tables
     SysView *views = nullptr;
     BatchRep *reps = nullptr;
     int2 *gmap = nullptr;
@@ -191,6 +194,7 @@ nb_status nb_batch_create(nb_ctx *const *ctxs, int n, nb_batch **out) {
         nb_ctx *c = ctxs[r];
         c->xq_cur = nullptr;  // the batched gather writes the context's own positions
         views[r] = nb_make_view(c, c->fs, nullptr, nullptr);
+        b->lj3 = b->lj3 && views[r].l3f != nullptr;
         BatchRep &p = reps[r];
         p.perm = c->perm;
         p.img = c->img;
@@ -223,9 +227,9 @@ nb_status nb_batch_create(nb_ctx *const *ctxs, int n, nb_batch **out) {
         nb_batch_destroy(b);
         return nb_cuda_status(err);
     }
-    const int occ = b->coulomb == NB_COULOMB_RF      ? occupancy<NB_COULOMB_RF, true, true>()
-                    : b->coulomb == NB_COULOMB_EWALD ? occupancy<NB_COULOMB_EWALD, true, true>()
-                                                     : occupancy<NB_COULOMB_NONE, true, true>();
+    const int occ = b->coulomb == NB_COULOMB_RF      ? occupancy<NB_COULOMB_RF, true, true>(b->lj3)
+                    : b->coulomb == NB_COULOMB_EWALD ? occupancy<NB_COULOMB_EWALD, true, true>(b->lj3)
+                                                     : occupancy<NB_COULOMB_NONE, true, true>(b->lj3);
     b->grid = std::max(1, std::min(sms * occ, ((int)items.size() + kBW - 1) / kBW));
     // queue order: all but the shortest items in system order (each system's items are
     // longest first in its list), then the shortest two per resident warp, longest first
@@ -277,8 +281,15 @@ nb_status nb_forces_batched(nb_batch *b, unsigned flags, const float *x, float *
     if (vi) NB_CUDA_TRY(cudaMemsetAsync(vir, 0, sizeof(double) * 9 * b->R, st));
     if (b->n_gblk > 0) k_batch_gather<<<b->n_gblk, kGatherBlock, 0, st>>>(b->reps, b->gblk, x);
     if (b->total_items > 0) {
-#define NB_BATCH_LAUNCH(C, E, V) \
-    k_forces_batched<C, E, V><<<b->grid, kBW * 32, 0, st>>>(b->views, b->reps, b->gmap, b->total_items, b->queue, e, vir)
+#define NB_BATCH_LAUNCH(C, E, V)                                                                               \
+    do {                                                                                                       \
+        if (b->lj3)                                                                                            \
+            k_forces_batched<C, E, V, true>                                                                    \
+                <<<b->grid, kBW * 32, 0, st>>>(b->views, b->reps, b->gmap, b->total_items, b->queue, e, vir);  \
+        else                                                                                                   \
+            k_forces_batched<C, E, V, false>                                                                   \
+                <<<b->grid, kBW * 32, 0, st>>>(b->views, b->reps, b->gmap, b->total_items, b->queue, e, vir);  \
+    } while (0)
         if (b->coulomb == NB_COULOMB_RF) {
             if (en && vi) NB_BATCH_LAUNCH(NB_COULOMB_RF, true, true);
             else if (en) NB_BATCH_LAUNCH(NB_COULOMB_RF, true, false);

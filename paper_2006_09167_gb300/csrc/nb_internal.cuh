@@ -28,6 +28,7 @@
 #define NB_SCL 8           // clusters per super-cluster (2x2x2)
 #define NB_SCA 64          // atoms per super-cluster
 #define NB_MAX_EXCL 16     // exclusion partners per atom
+#define NB_LJ3_MAX_T 8     // types up to which the T^3 parameter tables are kept (48 B x 512)
 #define NB_MAX_COL 8192    // atoms per grid column (bitonic sort in shared memory)
 #define NB_MAX_TYPES 64
 #define NB_PAD_COORD -1.0e5f
@@ -52,6 +53,8 @@ struct SysView {
     const unsigned short *mask_lanes;
     const float2 *lj;   // [T*T] (6*C6, 12*C12), symmetrised
     const float4 *lje;  // [T*T] (C6, C12, C12/rc^12 - C6/rc^6, 0), symmetrised
+    const float4 *l3f, *l3e;  // [T^3] or nullptr: (6 C6, 6 C6', 12 C12, 12 C12'), (C6, C6', C12, C12')
+    const float2 *l3s;        // [T^3] or nullptr: (shift, shift')
     float4 *f;          // sorted force accumulators
     double *e;          // [2] or nullptr
     double *vir;        // [9] or nullptr
@@ -135,6 +138,10 @@ struct nb_ctx {
     int *excl_off = nullptr, *excl_idx = nullptr;
     float2 *lj = nullptr;
     float4 *lje = nullptr;
+    // for at most NB_LJ3_MAX_T types: the same parameters by (i-type, j-type, j-type'),
+    // both pairs of a packed iteration in one entry (read by the batched kernel)
+    float4 *l3f = nullptr, *l3e = nullptr;
+    float2 *l3s = nullptr;
     // grid
     bool have_grid = false;
     double box[3] = {0, 0, 0};
