@@ -1,4 +1,6 @@
 """Batched persistent kernel (nb_forces_batched) against per-system nb_forces and the oracle."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -52,6 +54,43 @@ def test_batched_equals_plain(api, replicas):
         assert rel(e[2 * r + 1].item(), ep[1].item()) < 1e-9
         wb = w[9 * r:9 * r + 9].cpu().numpy()
         assert np.abs(wb - wp.cpu().numpy().ravel()).max() <= 1e-6 * np.abs(wp.cpu().numpy()).max()
+    for c in ctxs:
+        assert c.nb_get_error() == 0
+
+
+def test_batched_after_new_lj_tables(api, replicas):
+    """nb_set_lj on the contexts of a batch: the batched kernel reads the rearranged
+    (i-type, j-type, j-type') tables kept per context, which nb_set_lj rebuilds; the
+    single-system kernel forms them from the new T x T tables itself.  Both must agree,
+    and with the oracle run on the new tables."""
+    systems = replicas[:3]
+    ctxs, xs = build_all(api, systems)
+    rng = np.random.default_rng(17)
+    new_tables = []
+    for c, s in zip(ctxs, systems):
+        scale6 = rng.uniform(0.8, 1.2, s.c6.shape)
+        scale12 = rng.uniform(0.8, 1.2, s.c12.shape)
+        c6 = (s.c6 * (scale6 + scale6.T) / 2).astype(np.float32)
+        c12 = (s.c12 * (scale12 + scale12.T) / 2).astype(np.float32)
+        c.nb_set_lj(torch.tensor(c6, device="cuda"), torch.tensor(c12, device="cuda"))
+        new_tables.append((c6, c12))
+    plain = [c.forces(x, energy=True, virial=True) for c, x in zip(ctxs, xs)]
+    b = api.NbBatch(ctxs)
+    xcat = torch.cat(xs).contiguous()
+    f = torch.empty_like(xcat)
+    e = torch.empty(2 * len(ctxs), dtype=torch.float64, device="cuda")
+    w = torch.empty(9 * len(ctxs), dtype=torch.float64, device="cuda")
+    b.nb_forces_batched(api.NB_ENERGY | api.NB_VIRIAL, xcat, f, e, w)
+    torch.cuda.synchronize()
+    off = b.offsets
+    for r, (fp, ep, wp) in enumerate(plain):
+        assert_forces(f[off[r]:off[r + 1]].cpu().numpy(), fp.cpu().numpy(), tol_rms=1e-6, tol_atom=1e-5)
+        assert rel(e[2 * r].item(), ep[0].item()) < 1e-9
+    s0 = dataclasses.replace(systems[0], c6=new_tables[0][0], c12=new_tables[0][1])
+    ref = oracle.celllist(s0)
+    tol_lj, _ = energy_tolerances(s0, ref)
+    assert_forces(f[off[0]:off[1]].cpu().numpy(), ref)
+    assert rel(e[0].item(), ref["E_lj"]) < tol_lj
     for c in ctxs:
         assert c.nb_get_error() == 0
 
