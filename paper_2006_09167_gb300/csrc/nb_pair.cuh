@@ -28,6 +28,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// 2^x (the hardware approximation, flush-to-zero form)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float div_approx(float a, float b) {
     float r;
     asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
@@ -460,10 +467,10 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             const float4 xi = s_xi[k * NB_CL + ti];
             const float2 dx = psub(p2(xi.x), jx), dy = psub(p2(xi.y), jy), dz = psub(p2(xi.z), jz);
             const float2 qi2 = p2(xi.w);
-            if (PRUNE) {  // same distances, same rounding as the separate prune pass
-                const float2 r2 = pfma(dz, dz, pfma(dy, dy, pmul(dx, dx)));
-                keep_lo |= (int)__any_sync(full, r2.x < v.rin2) << k;
-                keep_hi |= (int)__any_sync(full, r2.y < v.rin2) << k;
+            if (PRUNE) {  // the separate prune pass's test, r^2 - r_in^2 < 0, rounded alike
+                const float2 q = pfma(dz, dz, pfma(dy, dy, pfma(dx, dx, p2(-v.rin2))));
+                keep_lo |= (int)__any_sync(full, __float_as_uint(q.x) >> 31) << k;
+                keep_hi |= (int)__any_sync(full, __float_as_uint(q.y) >> 31) << k;
             }
             const Lj2 lj = LJ3 ? lj_triple<EN>(ljt, tio * v.T + tjj) : lj_gather<EN>(ljt, tio + tj0, tio + tj1);
             const float2 p = pair_phi2<COUL, EN>(v, lj, dx, dy, dz, qi2, jq, b0, b1, elj2, ec2);

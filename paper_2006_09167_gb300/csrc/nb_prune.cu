@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunk
         const int2 ent = valid ? a.cj_outer[j0 + e] : make_int2(0, 0);
         const int im = ent.y & 0xff;
         // j-atoms b and b + 4 as packed pairs: component 0 decides the lower j-half,
-        // component 1 the upper (the force kernel's distances, rounded alike)
+        // component 1 the upper
         float2 jx[4], jy[4], jz[4];
 #pragma unroll
         for (int b = 0; b < 4; b++) {
@@ -83,16 +83,19 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunk
         for (int k = 0; k < NB_SCL; k++) {
             if (im & (1 << k)) {
                 const float4 xi = s_xi[wib][k * NB_CL + t];
-                bool any0 = false, any1 = false;
+                // q = r^2 - r_in^2 in one FMA chain: a pair is inside iff q's sign bit is set,
+                // so the test of 8 pairs is a bitwise OR (r_in carries a margin of 2e-6, far
+                // above the rounding of q, so every pair closer than r_in is kept)
+                unsigned s0 = 0u, s1 = 0u;
 #pragma unroll
                 for (int b = 0; b < 4; b++) {
                     const float2 dx = psub(p2(xi.x), jx[b]), dy = psub(p2(xi.y), jy[b]), dz = psub(p2(xi.z), jz[b]);
-                    const float2 r2 = pfma(dz, dz, pfma(dy, dy, pmul(dx, dx)));
-                    any0 |= r2.x < a.rin2;
-                    any1 |= r2.y < a.rin2;
+                    const float2 q = pfma(dz, dz, pfma(dy, dy, pfma(dx, dx, p2(-a.rin2))));
+                    s0 |= __float_as_uint(q.x);
+                    s1 |= __float_as_uint(q.y);
                 }
-                lo |= (int)any0 << k;
-                hi |= (int)any1 << k;
+                lo |= (int)(s0 >> 31) << k;
+                hi |= (int)(s1 >> 31) << k;
             }
         }
         int kept = lo | (hi << 8);

@@ -80,7 +80,7 @@ __device__ __forceinline__ bool vjp_pair(const VjpView &v, const float4 *__restr
     } else if (COUL == NB_COULOMB_EWALD) {
         const float r = r2 * rinv;
         const float z = sv.ew_beta * r;
-        const float ez = __expf(-z * z);
+        const float ez = ex2_approx(-z * z * 1.44269504f);  // exp(-z^2)
         const float ec = ez * ew_x(z * (1.0f / NB_EW_ZMAX));
         const float ex = v.two_beta_sqrtpi * ez;
         psi = f * fmaf(ec, rinv, ex) * rinv2;
