@@ -12,6 +12,7 @@
 
 nb_status nb_launch_grid_sort_phase1(nb_ctx *c, const float *x, cudaStream_t st);
 nb_status nb_launch_grid_sort_phase2(nb_ctx *c, int max_col, cudaStream_t st);
+int nb_search_units(int S);  // search units (super-cluster, column segment) for S super-clusters
 nb_status nb_launch_search_count(nb_ctx *c, float rlist, cudaStream_t st);
 nb_status nb_launch_search_write(nb_ctx *c, float rlist, cudaStream_t st);
 
@@ -444,8 +445,9 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     nb_status s;
     c->have_list = false;
-    if (c->S_host + 1 > c->si_cap) {
-        int cap = c->S_cap + 1;
+    const int units = nb_search_units(c->S_host);
+    if (units + 1 > c->si_cap) {
+        int cap = nb_search_units(c->S_cap) + 1;
         if ((s = dalloc(&c->si_counts, (size_t)cap * 4)) != NB_OK) return s;
         if ((s = dalloc(&c->si_offs, (size_t)(cap + 1) * 4)) != NB_OK) return s;
         c->si_cap = cap;
@@ -454,7 +456,7 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
     if ((long long)c->S_host * NB_SCL >= (1ll << 24)) return NB_ERR_CAPACITY;  // 24-bit cluster index
     if ((s = nb_launch_search_count(c, rlist, st)) != NB_OK) return s;
     int tot[4];
-    NB_CUDA_TRY(cudaMemcpyAsync(tot, c->si_offs + 4 * (size_t)c->S_host, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    NB_CUDA_TRY(cudaMemcpyAsync(tot, c->si_offs + 4 * (size_t)units, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     NB_CUDA_TRY(cudaStreamSynchronize(st));
     c->n_j = tot[0];
     c->n_items = tot[1];

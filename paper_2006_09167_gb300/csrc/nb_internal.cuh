@@ -179,8 +179,8 @@ struct nb_ctx {
     int2 *cj_outer = nullptr, *cj_inner = nullptr, *cj_tmp = nullptr;
     unsigned long long *masks = nullptr;
     unsigned short *mask_lanes = nullptr;  // [32 * masks_cap] the masks in lane order
-    int *si_counts = nullptr;  // [3*si_cap]: j entries, items, mask groups per super-cluster
-    int *si_offs = nullptr;    // [3*(si_cap+1)]
+    int *si_counts = nullptr;  // [4*si_cap]: j entries, items, mask groups, bits per search unit
+    int *si_offs = nullptr;    // [4*(si_cap+1)]
     int *sort_tmp = nullptr;   // item sort scratch
     unsigned short *kept = nullptr;  // [j_cap] prune scratch: surviving half masks per outer entry
     int sort_tmp_cap = 0;

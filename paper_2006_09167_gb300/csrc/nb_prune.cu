@@ -34,13 +34,14 @@ struct PruneArgs {
 //    i-atom t of every i-cluster) and writes each entry's surviving mask byte;
 //  k_prune_compact: one warp per item of this part copies the entries whose mask
 //    survived, in their original order, into the inner list.
-// When no item has more than one chunk (work items of at most 16 outer entries,
-// the usual split), the warp that prunes an item also compacts it (COMPACT):
-// one launch, and no round trip of the masks through memory.
-constexpr int kPruneChunk = 16;
+// Items of at most 64 entries (the usual splits) are one chunk: the warp that
+// prunes an item also compacts it (COMPACT), one launch and no round trip of the
+// masks through memory.
+constexpr int kPruneChunk = 16;     // entries per warp for items longer than kPruneWhole
+constexpr int kPruneWhole = 64;     // items up to this many entries: one warp prunes and compacts them
 
 template <bool COMPACT>
-__global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunks_per_item) {
+__global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunks_per_item, int chunk) {
     __shared__ float4 s_xi[kPW][NB_SCA];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
@@ -48,12 +49,12 @@ __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunk
     const long long item = a.part + (w / chunks_per_item) * a.n_parts;
     if (item >= a.n_items) return;
     const int4 it = a.items[item];
-    const int e_begin = (int)(w % chunks_per_item) * kPruneChunk;
+    const int e_begin = (int)(w % chunks_per_item) * chunk;
     if (e_begin >= it.w) {
         if (COMPACT && lane == 0) a.inner_len[item] = 0;
         return;
     }
-    const int e_end = min(it.w, e_begin + kPruneChunk);
+    const int e_end = min(it.w, e_begin + chunk);
     const int si = it.x, sidx = it.y, j0 = it.z;
     const ShiftSplit sh = make_shift(sidx, a.Lhi, a.Llo);
     for (int h = 0; h < 2; h++) {
@@ -268,15 +269,18 @@ nb_status nb_launch_prune(nb_ctx *c, float r_in, int part, int n_parts, cudaStre
     a.kept = c->kept;
     long long nw = (c->n_items - part + n_parts - 1) / n_parts;
     if (nw <= 0) return NB_OK;
-    const int chunks = (c->split_built + kPruneChunk - 1) / kPruneChunk;
+    // items of at most kPruneWhole entries: one warp per item, pruned and compacted in one
+    // pass; longer ones: chunks of kPruneChunk entries, then a compaction kernel
+    const int chunk = c->split_built <= kPruneWhole ? std::max(c->split_built, 1) : kPruneChunk;
+    const int chunks = (c->split_built + chunk - 1) / chunk;
     NbTraceScope tr(c, NB_TRACE_PRUNE, st);
     c->n_launches += 2;
     const long long nwm = nw * chunks;
     if (chunks == 1) {  // an item fits one chunk: prune and compact in one pass
         c->n_launches--;
-        k_prune_masks<true><<<(unsigned)((nwm + kPW - 1) / kPW), kPW * 32, 0, st>>>(a, chunks);
+        k_prune_masks<true><<<(unsigned)((nwm + kPW - 1) / kPW), kPW * 32, 0, st>>>(a, chunks, chunk);
     } else {
-        k_prune_masks<false><<<(unsigned)((nwm + kPW - 1) / kPW), kPW * 32, 0, st>>>(a, chunks);
+        k_prune_masks<false><<<(unsigned)((nwm + kPW - 1) / kPW), kPW * 32, 0, st>>>(a, chunks, chunk);
         k_prune_compact<<<(unsigned)((nw + kPW - 1) / kPW), kPW * 32, 0, st>>>(a);
     }
     NB_CUDA_TRY(cudaGetLastError());

@@ -12,7 +12,10 @@
 //
 // The search runs twice: a counting pass sizes every super-cluster's output,
 // an exclusive scan turns the counts into offsets, and a writing pass emits
-// entries in a fixed order, so the list is deterministic.
+// entries in a fixed order, so the list is deterministic.  Each super-cluster
+// is searched by kSeg warps, warp g taking the grid columns with index = g
+// (mod kSeg); each (super-cluster, segment) has its own count and offset, and
+// its work items hold the entries of one shift and one segment.
 #include "nb_internal.cuh"
 
 using namespace nbk;
@@ -20,6 +23,7 @@ using namespace nbk;
 namespace {
 
 constexpr int kWarps = 4;
+constexpr int kSeg = 2;  // warps per super-cluster (column segments)
 
 struct SearchArgs {
     int S;
@@ -51,7 +55,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_search(SearchArgs a) {
     __shared__ int s_pcnt[kWarps][NB_SCA];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int si = blockIdx.x * kWarps + wib;
+    const int unit = blockIdx.x * kWarps + wib;  // (super-cluster, column segment)
+    const int si = unit / kSeg, seg = unit % kSeg;
     if (si >= a.S) return;
     const unsigned full = 0xffffffffu;
 
@@ -82,9 +87,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_search(SearchArgs a) {
     int n_j = 0, n_items = 0, n_masks = 0, n_bits = 0;
     int j_base = 0, it_base = 0, m_base = 0;
     if (WRITE) {
-        j_base = a.si_offs[4 * si + 0];
-        it_base = a.si_offs[4 * si + 1];
-        m_base = a.si_offs[4 * si + 2];
+        j_base = a.si_offs[4 * unit + 0];
+        it_base = a.si_offs[4 * unit + 1];
+        m_base = a.si_offs[4 * unit + 2];
     }
 
     for (int sidx = 0; sidx < 27; sidx++) {
@@ -115,6 +120,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_search(SearchArgs a) {
         for (int ix = ix0; ix <= ix1; ix++) {
             for (int iy = iy0; iy <= iy1; iy++) {
                 const int col = ix * a.ncy + iy;
+                if (col % kSeg != seg) continue;
                 const int sa = max(a.col_sc_off[col], si), sb = a.col_sc_off[col + 1];
                 for (int c0 = sa; c0 < sb; c0 += 32) {
                     const int sj = c0 + lane;
@@ -213,10 +219,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_search(SearchArgs a) {
         }
     }
     if (!WRITE && lane == 0) {
-        a.si_counts[4 * si + 0] = n_j;
-        a.si_counts[4 * si + 1] = n_items;
-        a.si_counts[4 * si + 2] = n_masks;
-        a.si_counts[4 * si + 3] = n_bits;
+        a.si_counts[4 * unit + 0] = n_j;
+        a.si_counts[4 * unit + 1] = n_items;
+        a.si_counts[4 * unit + 2] = n_masks;
+        a.si_counts[4 * unit + 3] = n_bits;
     }
 }
 
@@ -336,6 +342,9 @@ __global__ void k_item_scatter(int n, int split, const int4 *__restrict__ in, co
 
 }  // namespace
 
+// search units (super-cluster, column segment): the length of the count and offset arrays / 4
+int nb_search_units(int S) { return S * kSeg; }
+
 static SearchArgs make_args(nb_ctx *c, float rlist) {
     SearchArgs a;
     a.S = c->S_host;
@@ -366,17 +375,18 @@ static SearchArgs make_args(nb_ctx *c, float rlist) {
 
 nb_status nb_launch_search_count(nb_ctx *c, float rlist, cudaStream_t st) {
     SearchArgs a = make_args(c, rlist);
-    int nblk = (c->S_host + kWarps - 1) / kWarps;
+    const int units = c->S_host * kSeg;
+    int nblk = (units + kWarps - 1) / kWarps;
     c->n_launches += 2;
     k_search<false><<<nblk, kWarps * 32, 0, st>>>(a);
-    k_scan4<<<1, 1024, 0, st>>>(c->S_host, c->si_counts, c->si_offs);
+    k_scan4<<<1, 1024, 0, st>>>(units, c->si_counts, c->si_offs);
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
 }
 
 nb_status nb_launch_search_write(nb_ctx *c, float rlist, cudaStream_t st) {
     SearchArgs a = make_args(c, rlist);
-    int nblk = (c->S_host + kWarps - 1) / kWarps;
+    int nblk = (c->S_host * kSeg + kWarps - 1) / kWarps;
     c->n_launches++;
     k_search<true><<<nblk, kWarps * 32, 0, st>>>(a);
     NB_CUDA_TRY(cudaGetLastError());
