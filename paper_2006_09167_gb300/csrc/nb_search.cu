@@ -23,7 +23,7 @@ using namespace nbk;
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kSeg = 2;  // warps per super-cluster (column segments)
+constexpr int kSeg = 8;  // warps per super-cluster (column segments)
 
 struct SearchArgs {
     int S;
