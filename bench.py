@@ -405,12 +405,13 @@ def extra_workloads(args):
     from paper_2006_09167_gb300 import autotune
     flush = l2_flusher(dev)
     xs_tune = [torch.tensor(sysr.x, device=dev) for sysr in reps]
-    tuned_b = autotune.tune_batched(reps, xs_tune, splits=(16, 24, 32, 48, 64, 96, 128), reps=5, flush=flush)
+    tuned_b = autotune.tune_batched(reps, xs_tune, splits=(16, 32, 64, 96, 128), reps=5, flush=flush, segments=(0, 1))
     del xs_tune
     ctxs, xs = [], []
     for sysr in reps:
         c = api.NbContext.from_system(sysr)
         c.nb_set_split(tuned_b["split"])
+        c.nb_set_search_segments(tuned_b["segments"])
         xr = torch.tensor(sysr.x, device=dev)
         c.build(xr, sysr.box)
         ctxs.append(c)
@@ -483,6 +484,7 @@ def extra_workloads(args):
     t_plain_seq = time_fn(plain_fn(ctxs_p), reps_=5, warm=1)
     out["batched_256_replicas"] = {
         "atoms_total": int(n_all), "replicas": R, "split_autotuned": int(tuned_b["split"]),
+        "search_segments_autotuned": int(tuned_b["segments"]),
         "split_plain_best": int(split_plain),
         "batched_graph_ms": t_batched_graph, "plain_graph_ms": t_plain_graph, "plain_sequential_ms": t_plain_seq,
         "system_evals_per_s_batched": R * 1e3 / t_batched_graph,

@@ -265,6 +265,17 @@ nb_status nb_set_fused_prune(nb_ctx *ctx, int on);
  * 16).  Takes effect at the next nb_pairlist_build. */
 nb_status nb_set_split(nb_ctx *ctx, int max_entries_per_item);
 
+/* Tuning (not in the paper): the number of column segments of the pair search,
+ * 1..8, or 0 (the default) for the library's choice.  Each super-cluster's
+ * j-list is searched by that many warps, warp g taking the grid columns with
+ * index = g (mod segments), and each work item then holds the entries of one
+ * shift and one segment.  The library's choice doubles the segments from 1 while
+ * the search would have fewer than 12,000 warps (8 for a 96k-atom water box, 1
+ * for 1.5M atoms).  The pair set is the same for every value; the item structure,
+ * and with it the work balance of the force kernels, is not.  Takes effect at the
+ * next nb_pairlist_build; NB_ERR_INVALID_ARG outside 0..8. */
+nb_status nb_set_search_segments(nb_ctx *ctx, int segments);
+
 /* Tracing (not in the paper): CUDA events are recorded on the launch stream
  * around every kernel of the kinds selected by `kinds` (bit NB_TRACE_x set:
  * kind x is traced; 0 turns tracing off; other bits: NB_ERR_INVALID_ARG) of

@@ -37,6 +37,7 @@ EXPORTED = [
     "nb_get_stats", "nb_get_error", "nb_status_str", "nb_trace_enable", "nb_trace_read",
     "nb_forces_small_noalloc", "nb_set_split", "nb_pme_create", "nb_pme_destroy", "nb_pme_forces",
     "nb_ewald_corrections", "nb_set_fused_prune", "nb_sorted_export", "nb_forces_sorted", "nb_forces_vjp_dev",
+    "nb_set_search_segments",
 ]
 NB_NOALLOC_MAX_ATOMS = 16384
 NB_NOALLOC_MAX_TYPES = 8
@@ -117,6 +118,7 @@ def load(path: str = LIB_PATH):
     lib.nb_get_stats.argtypes = [vp, ctypes.POINTER(NbStats)]
     lib.nb_get_error.argtypes = [vp, vp]
     lib.nb_set_split.argtypes = [vp, ctypes.c_int]
+    lib.nb_set_search_segments.argtypes = [vp, ctypes.c_int]
     lib.nb_set_fused_prune.argtypes = [vp, ctypes.c_int]
     lib.nb_trace_enable.argtypes = [vp, ctypes.c_int]
     lib.nb_trace_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p]

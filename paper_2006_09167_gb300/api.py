@@ -214,6 +214,10 @@ class NbContext:
     def nb_set_split(self, split: int):
         check(self._lib.nb_set_split(self.handle, int(split)), "nb_set_split")
 
+    def nb_set_search_segments(self, segments: int):
+        """Column segments of the pair search, 1..8, or 0 for the library's choice (nb_set_search_segments)."""
+        check(self._lib.nb_set_search_segments(self.handle, int(segments)), "nb_set_search_segments")
+
     def nb_trace_enable(self, enable: bool = True, kinds=None):
         """Time launches with CUDA events: every kind (kinds=None) or the listed
         NB_TRACE_* kinds; enable=False turns tracing off."""

@@ -148,11 +148,14 @@ def tune(system, x, velocities=None, *, splits: Sequence[int] = SPLITS, parts: S
 
 
 def tune_batched(systems, xs, *, splits: Sequence[int] = SPLITS, reps: int = 10, flags: Optional[int] = None,
-                 flush: Optional[Callable[[], None]] = None) -> dict:
-    """Tune the split of a batched evaluation (nb_forces_batched) by timing the
-    batched launch itself over `systems` at positions `xs` (CUDA float32 [N_r,3]
-    each): the best item size for many systems sharing the GPU differs from the
-    best one for any of them alone.  Returns {"split", "split_ms"}."""
+                 flush: Optional[Callable[[], None]] = None, segments: Sequence[int] = (0,)) -> dict:
+    """Tune the split (and, given several `segments` values, the pair search's column
+    segments, 0 = the library's choice) of a batched evaluation (nb_forces_batched) by
+    timing the batched launch itself over `systems` at positions `xs` (CUDA float32
+    [N_r,3] each): the best item size for many systems sharing the GPU differs from the
+    best one for any of them alone.  Returns {"split", "segments", "split_ms"} with
+    split_ms the timings of the chosen segments value, and "timings" {(segments,
+    split): ms}."""
     import torch
 
     from . import api
@@ -165,28 +168,32 @@ def tune_batched(systems, xs, *, splits: Sequence[int] = SPLITS, reps: int = 10,
     r = len(systems)
     e = torch.empty(2 * r, dtype=torch.float64, device=dev)
     w = torch.empty(9 * r, dtype=torch.float64, device=dev)
-    split_ms = {}
-    for sp in splits:
-        ctxs = []
-        for s, xr in zip(systems, xs):
-            c = api.NbContext.from_system(s)
-            c.nb_set_split(sp)
-            c.build(xr, s.box)
-            ctxs.append(c)
-        b = api.NbBatch(ctxs)
-        for _ in range(3):
-            b.nb_forces_batched(flags, xcat, fcat, e, w)
-        tot = 0.0
-        for _ in range(reps):
-            if flush is not None:
-                flush()
-            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            t0.record()
-            b.nb_forces_batched(flags, xcat, fcat, e, w)
-            t1.record()
-            t1.synchronize()
-            tot += t0.elapsed_time(t1)
-        split_ms[sp] = tot / reps
-        b.close()
-        del ctxs
-    return {"split": choose_split(split_ms), "split_ms": split_ms}
+    timings = {}
+    for seg in segments:
+        for sp in splits:
+            ctxs = []
+            for s, xr in zip(systems, xs):
+                c = api.NbContext.from_system(s)
+                c.nb_set_split(sp)
+                c.nb_set_search_segments(seg)
+                c.build(xr, s.box)
+                ctxs.append(c)
+            b = api.NbBatch(ctxs)
+            for _ in range(3):
+                b.nb_forces_batched(flags, xcat, fcat, e, w)
+            tot = 0.0
+            for _ in range(reps):
+                if flush is not None:
+                    flush()
+                t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0.record()
+                b.nb_forces_batched(flags, xcat, fcat, e, w)
+                t1.record()
+                t1.synchronize()
+                tot += t0.elapsed_time(t1)
+            timings[(seg, sp)] = tot / reps
+            b.close()
+            del ctxs
+    best_seg = min(segments, key=lambda g: (min(timings[(g, sp)] for sp in splits), g))
+    split_ms = {sp: timings[(best_seg, sp)] for sp in splits}
+    return {"split": choose_split(split_ms), "segments": best_seg, "split_ms": split_ms, "timings": timings}

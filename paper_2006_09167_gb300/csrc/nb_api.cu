@@ -12,7 +12,7 @@
 
 nb_status nb_launch_grid_sort_phase1(nb_ctx *c, const float *x, cudaStream_t st);
 nb_status nb_launch_grid_sort_phase2(nb_ctx *c, int max_col, cudaStream_t st);
-int nb_search_units(int S);  // search units (super-cluster, column segment) for S super-clusters
+int nb_search_units(const nb_ctx *c);  // search units (super-cluster, column segment) of the next build
 nb_status nb_launch_search_count(nb_ctx *c, float rlist, cudaStream_t st);
 nb_status nb_launch_search_write(nb_ctx *c, float rlist, cudaStream_t st);
 
@@ -445,9 +445,9 @@ nb_status nb_pairlist_build(nb_ctx *c, float rlist, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     nb_status s;
     c->have_list = false;
-    const int units = nb_search_units(c->S_host);
+    const int units = nb_search_units(c);
     if (units + 1 > c->si_cap) {
-        int cap = nb_search_units(c->S_cap) + 1;
+        int cap = units + units / 8 + 1;
         if ((s = dalloc(&c->si_counts, (size_t)cap * 4)) != NB_OK) return s;
         if ((s = dalloc(&c->si_offs, (size_t)(cap + 1) * 4)) != NB_OK) return s;
         c->si_cap = cap;
@@ -641,6 +641,13 @@ nb_status nb_set_fused_prune(nb_ctx *c, int on) {
 nb_status nb_set_split(nb_ctx *c, int split) {
     if (!c || split < 4 || split > 128) return NB_ERR_INVALID_ARG;
     c->split = split;
+    c->have_list = false;  // the item structure changes with the next build
+    return NB_OK;
+}
+
+nb_status nb_set_search_segments(nb_ctx *c, int segments) {
+    if (!c || segments < 0 || segments > 8) return NB_ERR_INVALID_ARG;
+    c->search_seg = segments;
     c->have_list = false;  // the item structure changes with the next build
     return NB_OK;
 }

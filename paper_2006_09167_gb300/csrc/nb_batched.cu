@@ -67,13 +67,15 @@ __global__ void __launch_bounds__(kBW * 32)
             __syncwarp();
             if (EN || VIR) {
                 warp_reduce_outputs<EN, VIR>(elj, ec, vr);
-                if (lane == 0) {
-                    if (EN) {
-                        atomicAdd(&e[2 * m.x], (double)elj.s - (double)elj.c);
-                        atomicAdd(&e[2 * m.x + 1], reps[m.x].coul_f * ((double)ec.s - (double)ec.c));
-                    }
-                    if (VIR)
-                        for (int k = 0; k < 9; k++) atomicAdd(&vir[9 * m.x + k], -0.5 * (double)vr[k]);
+                // every lane holds the totals: lanes 0-1 add the energies, lanes 2-10 the virial
+                if (EN && lane < 2)
+                    atomicAdd(&e[2 * m.x + lane], lane == 0 ? (double)elj.s - (double)elj.c
+                                                            : reps[m.x].coul_f * ((double)ec.s - (double)ec.c));
+                if (VIR && lane >= 2 && lane < 11) {
+                    float val = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 9; k++) val = (lane - 2 == k) ? vr[k] : val;
+                    atomicAdd(&vir[9 * m.x + lane - 2], -0.5 * (double)val);
                 }
             }
         }

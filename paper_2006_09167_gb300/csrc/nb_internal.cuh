@@ -171,6 +171,7 @@ struct nb_ctx {
     bool fused_prune = false;    // first prune after a build inside the first force call
     bool inner_pending = false;  // the inner list awaits that first prune
     int split = 16;          // max outer j-entries per work item (next build)
+    int search_seg = 0;      // column segments of the pair search (0: the library's choice; next build)
     int split_built = 16;    // max outer j-entries per work item of the current lists
     int n_items = 0, n_j = 0, n_masks = 0;
     int items_cap = 0, j_cap = 0, masks_cap = 0, si_cap = 0;

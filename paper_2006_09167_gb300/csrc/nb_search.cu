@@ -13,8 +13,9 @@
 // The search runs twice: a counting pass sizes every super-cluster's output,
 // an exclusive scan turns the counts into offsets, and a writing pass emits
 // entries in a fixed order, so the list is deterministic.  Each super-cluster
-// is searched by kSeg warps, warp g taking the grid columns with index = g
-// (mod kSeg); each (super-cluster, segment) has its own count and offset, and
+// is searched by `seg` warps (1 to 8: enough warps to fill the GPU when there
+// are few super-clusters), warp g taking the grid columns with index = g
+// (mod seg); each (super-cluster, segment) has its own count and offset, and
 // its work items hold the entries of one shift and one segment.
 #include "nb_internal.cuh"
 
@@ -23,7 +24,8 @@ using namespace nbk;
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kSeg = 8;  // warps per super-cluster (column segments)
+constexpr int kSegMax = 8;          // most warps (column segments) per super-cluster
+constexpr int kSegWarps = 12000;    // segments are doubled while the search has fewer warps than this
 
 struct SearchArgs {
     int S;
@@ -35,6 +37,7 @@ struct SearchArgs {
     float rlist, rlist2;
     const int *perm, *inv, *excl_off, *excl_idx;
     int split;
+    int seg;             // column segments (warps) per super-cluster
     int *si_counts;      // count pass: [4*S] j entries, items, mask groups, mask bits
     const int *si_offs;  // write pass: [4*(S+1)] exclusive offsets
     int4 *items;
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_search(SearchArgs a) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int unit = blockIdx.x * kWarps + wib;  // (super-cluster, column segment)
-    const int si = unit / kSeg, seg = unit % kSeg;
+    const int si = unit / a.seg, seg = unit % a.seg;
     if (si >= a.S) return;
     const unsigned full = 0xffffffffu;
 
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_search(SearchArgs a) {
         for (int ix = ix0; ix <= ix1; ix++) {
             for (int iy = iy0; iy <= iy1; iy++) {
                 const int col = ix * a.ncy + iy;
-                if (col % kSeg != seg) continue;
+                if (col % a.seg != seg) continue;
                 const int sa = max(a.col_sc_off[col], si), sb = a.col_sc_off[col + 1];
                 for (int c0 = sa; c0 < sb; c0 += 32) {
                     const int sj = c0 + lane;
@@ -343,7 +346,14 @@ __global__ void k_item_scatter(int n, int split, const int4 *__restrict__ in, co
 }  // namespace
 
 // search units (super-cluster, column segment): the length of the count and offset arrays / 4
-int nb_search_units(int S) { return S * kSeg; }
+int nb_search_segments(const nb_ctx *c) {
+    if (c->search_seg > 0) return std::min(c->search_seg, kSegMax);
+    int seg = 1;
+    while (seg < kSegMax && (long long)c->S_host * seg < kSegWarps) seg *= 2;
+    return seg;
+}
+
+int nb_search_units(const nb_ctx *c) { return c->S_host * nb_search_segments(c); }
 
 static SearchArgs make_args(nb_ctx *c, float rlist) {
     SearchArgs a;
@@ -365,6 +375,7 @@ static SearchArgs make_args(nb_ctx *c, float rlist) {
     a.excl_off = c->excl_off;
     a.excl_idx = c->excl_idx;
     a.split = c->split;
+    a.seg = nb_search_segments(c);
     a.si_counts = c->si_counts;
     a.si_offs = c->si_offs;
     a.items = c->items_tmp;
@@ -375,7 +386,7 @@ static SearchArgs make_args(nb_ctx *c, float rlist) {
 
 nb_status nb_launch_search_count(nb_ctx *c, float rlist, cudaStream_t st) {
     SearchArgs a = make_args(c, rlist);
-    const int units = c->S_host * kSeg;
+    const int units = nb_search_units(c);
     int nblk = (units + kWarps - 1) / kWarps;
     c->n_launches += 2;
     k_search<false><<<nblk, kWarps * 32, 0, st>>>(a);
@@ -386,7 +397,7 @@ nb_status nb_launch_search_count(nb_ctx *c, float rlist, cudaStream_t st) {
 
 nb_status nb_launch_search_write(nb_ctx *c, float rlist, cudaStream_t st) {
     SearchArgs a = make_args(c, rlist);
-    int nblk = (c->S_host * kSeg + kWarps - 1) / kWarps;
+    int nblk = (nb_search_units(c) + kWarps - 1) / kWarps;
     c->n_launches++;
     k_search<true><<<nblk, kWarps * 32, 0, st>>>(a);
     NB_CUDA_TRY(cudaGetLastError());

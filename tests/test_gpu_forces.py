@@ -119,6 +119,39 @@ def test_pairlist_coverage_polymer_like_exclusions(api):
     assert not any((g[0], g[1]) in ex for g in got)
 
 
+def test_search_segments_same_pairs(api):
+    """The pair search's column segments change the work items, not the pair set:
+    outer and inner lists export the same image pairs for 1, 3 and 8 segments as
+    for the library's choice, and the forces agree."""
+    s = synth.polymer_water_box(seed=6, n_chain=4, chain_len=40, n_water=1200, box_len=3.4,
+                                water_side=11, rc=1.0, rlist=1.1)
+    xt = torch.tensor(s.x, device="cuda")
+    ref = None
+    for seg in (0, 1, 3, 8):
+        ctx = api.NbContext.from_system(s)
+        ctx.nb_set_search_segments(seg)
+        ctx.build(xt, s.box)
+        outer = canonical_pairs(ctx.nb_debug_export_pairs(api.NB_LIST_OUTER))
+        inner = canonical_pairs(ctx.nb_debug_export_pairs(api.NB_LIST_INNER))
+        f, e, _ = ctx.forces(xt, energy=True)
+        torch.cuda.synchronize()
+        got = (set(outer), set(inner), f.cpu().numpy(), e.cpu().numpy())
+        assert len(outer) == len(got[0]) and len(inner) == len(got[1])
+        if ref is None:
+            ref = got
+            continue
+        assert got[0] == ref[0] and got[1] == ref[1], f"segments {seg}: different pair set"
+        assert_forces(got[2], ref[2], tol_rms=1e-6, tol_atom=1e-5)
+        # other items sum the per-lane FP32 energy terms in another order: the totals agree to
+        # the FP32 summation error (amplified by the Coulomb sum's cancellation), within 1e-6
+        assert rel(got[3][0], ref[3][0]) < 1e-6 and rel(got[3][1], ref[3][1]) < 1e-6
+        assert ctx.nb_get_error() == 0
+    ctx = api.NbContext.from_system(s)
+    for bad in (-1, 9):
+        with pytest.raises(api.NbError):
+            ctx.nb_set_search_segments(bad)
+
+
 # ----------------------------------------------------------------- forces
 def test_forces_648_reaction_field(api):
     s = synth.water_648()
