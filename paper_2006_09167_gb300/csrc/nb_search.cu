@@ -12,11 +12,10 @@
 //
 // The search runs twice: a counting pass sizes every super-cluster's output,
 // an exclusive scan turns the counts into offsets, and a writing pass emits
-// entries in a fixed order, so the list is deterministic.  Each super-cluster
-// is searched by `seg` warps (1 to 8: enough warps to fill the GPU when there
-// are few super-clusters), warp g taking the grid columns with index = g
-// (mod seg); each (super-cluster, segment) has its own count and offset, and
-// its work items hold the entries of one shift and one segment.
+// entries in a fixed order, so the list is deterministic.  Each super-cluster's
+// grid columns are split into `seg` segments (1 to 8; column index mod seg), each
+// a search unit with its own count and offset searched by one warp, and work
+// items hold the entries of one shift and one segment.
 #include "nb_internal.cuh"
 
 using namespace nbk;
@@ -37,7 +36,7 @@ struct SearchArgs {
     float rlist, rlist2;
     const int *perm, *inv, *excl_off, *excl_idx;
     int split;
-    int seg;             // column segments (warps) per super-cluster
+    int seg;             // column segments (one warp each) per super-cluster
     int *si_counts;      // count pass: [4*S] j entries, items, mask groups, mask bits
     const int *si_offs;  // write pass: [4*(S+1)] exclusive offsets
     int4 *items;
@@ -229,35 +228,60 @@ __global__ void __launch_bounds__(kWarps * 32) k_search(SearchArgs a) {
     }
 }
 
-// Exclusive scan of 4 interleaved int streams of length n (one block); offs[4*n..4*n+3] = totals.
+// Exclusive scan of 4 interleaved int streams of length n (one block of 1024 threads);
+// offs[4*n..4*n+3] = totals.  Thread t sums a contiguous run of the units, a
+// shuffle scan over the block turns the run sums into run offsets, and each thread
+// then writes its run's offsets.
 __global__ void k_scan4(int n, const int *__restrict__ cnt, int *__restrict__ offs) {
-    __shared__ int s[4][1024];
-    __shared__ int carry[4];
-    if (threadIdx.x < 4) carry[threadIdx.x] = 0;
-    __syncthreads();
-    for (int base = 0; base < n; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        int v[4];
-        for (int k = 0; k < 4; k++) {
-            v[k] = i < n ? cnt[4 * i + k] : 0;
-            s[k][threadIdx.x] = v[k];
-        }
-        __syncthreads();
-        for (int d = 1; d < blockDim.x; d <<= 1) {
-            int t[4];
-            for (int k = 0; k < 4; k++) t[k] = threadIdx.x >= d ? s[k][threadIdx.x - d] : 0;
-            __syncthreads();
-            for (int k = 0; k < 4; k++) s[k][threadIdx.x] += t[k];
-            __syncthreads();
-        }
-        if (i < n)
-            for (int k = 0; k < 4; k++) offs[4 * i + k] = carry[k] + s[k][threadIdx.x] - v[k];
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1)
-            for (int k = 0; k < 4; k++) carry[k] += s[k][threadIdx.x];
-        __syncthreads();
+    __shared__ int4 s_warp[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b = min(n, t * per), e = min(n, b + per);
+    const int4 *c4 = reinterpret_cast<const int4 *>(cnt);
+    int4 sum = make_int4(0, 0, 0, 0);
+#pragma unroll 8
+    for (int i = b; i < e; i++) {
+        const int4 v = c4[i];
+        sum = make_int4(sum.x + v.x, sum.y + v.y, sum.z + v.z, sum.w + v.w);
     }
-    if (threadIdx.x < 4) offs[4 * n + threadIdx.x] = carry[threadIdx.x];
+    // inclusive scan of the run sums within the warp, then over the warps
+    int4 inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, inc.x, o), y = __shfl_up_sync(0xffffffffu, inc.y, o);
+        const int z = __shfl_up_sync(0xffffffffu, inc.z, o), w = __shfl_up_sync(0xffffffffu, inc.w, o);
+        if (lane >= o) inc = make_int4(inc.x + x, inc.y + y, inc.z + z, inc.w + w);
+    }
+    if (lane == 31) s_warp[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int4 v = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, v.x, o), y = __shfl_up_sync(0xffffffffu, v.y, o);
+            const int z = __shfl_up_sync(0xffffffffu, v.z, o), w = __shfl_up_sync(0xffffffffu, v.w, o);
+            if (lane >= o) v = make_int4(v.x + x, v.y + y, v.z + z, v.w + w);
+        }
+        s_warp[lane] = v;  // inclusive over warps
+    }
+    __syncthreads();
+    const int4 wbase = wid > 0 ? s_warp[wid - 1] : make_int4(0, 0, 0, 0);
+    int4 run = make_int4(wbase.x + inc.x - sum.x, wbase.y + inc.y - sum.y, wbase.z + inc.z - sum.z,
+                         wbase.w + inc.w - sum.w);
+    int4 *o4 = reinterpret_cast<int4 *>(offs);
+#pragma unroll 8
+    for (int i = b; i < e; i++) {
+        o4[i] = run;
+        const int4 v = c4[i];
+        run = make_int4(run.x + v.x, run.y + v.y, run.z + v.z, run.w + v.w);
+    }
+    if (t == blockDim.x - 1) {
+        const int4 tot = s_warp[(blockDim.x >> 5) - 1];
+        offs[4 * n] = tot.x;
+        offs[4 * n + 1] = tot.y;
+        offs[4 * n + 2] = tot.z;
+        offs[4 * n + 3] = tot.w;
+    }
 }
 
 // ---- stable counting sort of items by length, longest first (Sec. V.F) ----
