@@ -47,6 +47,8 @@ __global__ void __launch_bounds__(kBW * 32)
     __shared__ float4 s_xi[kBW][NB_SCA];
     __shared__ int s_ti[kBW][NB_SCA];
     __shared__ float s_fi[kBW][3 * NB_SCL * 32];
+    // the current item's system view, staged per warp (read from shared memory as needed)
+    __shared__ __align__(16) unsigned char s_view[kBW][sizeof(SysView)];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
     // first item: the warp's index in the grid; later items from the counter
@@ -54,7 +56,14 @@ __global__ void __launch_bounds__(kBW * 32)
     int g = blockIdx.x * kBW + wib;
     while (g < total) {
         const int2 m = gmap[g];
-        const SysView &v = views[m.x];
+        {
+            static_assert(sizeof(SysView) % 4 == 0, "view size");
+            const unsigned *src = reinterpret_cast<const unsigned *>(views + m.x);
+            unsigned *dst = reinterpret_cast<unsigned *>(s_view[wib]);
+            for (int k = lane; k < (int)(sizeof(SysView) / 4); k += 32) dst[k] = src[k];
+            __syncwarp();
+        }
+        const SysView &v = *reinterpret_cast<const SysView *>(s_view[wib]);
         const int nj = v.inner_len[m.y];
         if (nj > 0) {
             KSum elj, ec;
