@@ -829,6 +829,7 @@ def main_profile(args):
         for sysr in reps:
             c = api.NbContext.from_system(sysr)
             c.nb_set_split(args.split or 64)
+            c.nb_set_search_segments(1)  # unsegmented lists, as the batched autotuner picks
             xr = torch.tensor(sysr.x, device="cuda")
             c.build(xr, sysr.box)
             ctxs.append(c)

@@ -95,6 +95,33 @@ def test_batched_after_new_lj_tables(api, replicas):
         assert c.nb_get_error() == 0
 
 
+def test_batched_same_results_for_any_search_segments(api, replicas):
+    """Lists built with one and with eight column segments (other work items, same pairs)
+    give the batched kernel the same forces and energies."""
+    systems = replicas[:4]
+    outs = []
+    for seg in (1, 8):
+        ctxs, xs = [], []
+        for sysr in systems:
+            c = api.NbContext.from_system(sysr)
+            c.nb_set_search_segments(seg)
+            x = torch.tensor(sysr.x, device="cuda")
+            c.build(x, sysr.box)
+            ctxs.append(c)
+            xs.append(x)
+        b = api.NbBatch(ctxs)
+        xcat = torch.cat(xs).contiguous()
+        f = torch.empty_like(xcat)
+        e = torch.empty(2 * len(ctxs), dtype=torch.float64, device="cuda")
+        b.nb_forces_batched(api.NB_ENERGY, xcat, f, e)
+        torch.cuda.synchronize()
+        outs.append((f.cpu().numpy(), e.cpu().numpy()))
+        assert all(c.nb_get_error() == 0 for c in ctxs)
+    assert_forces(outs[1][0], outs[0][0], tol_rms=1e-6, tol_atom=1e-5)
+    # per-lane FP32 energy terms summed in other orders: agreement to the FP32 summation error
+    assert np.all(np.abs(outs[1][1] - outs[0][1]) <= 1e-6 * np.abs(outs[0][1]))
+
+
 def test_batched_oracle_parity_and_graph_replay(api, replicas):
     ctxs, xs = build_all(api, replicas)
     b = api.NbBatch(ctxs)
