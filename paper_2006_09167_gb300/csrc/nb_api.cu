@@ -138,6 +138,7 @@ nbk::SysView nb_make_view(const nb_ctx *c, float4 *f, double *e, double *vir) {
     v.rc6inv = (float)rc6;
     v.rc12inv = (float)(rc6 * rc6);
     v.queue = c->queue;
+    v.erow = c->erow;
     v.kept = nullptr;
     v.rin2 = 0.f;
     v.ew_beta2 = (float)(c->beta * c->beta);
@@ -252,7 +253,8 @@ nb_status nb_create(const nb_params *p, const float *q_host, const int32_t *type
     NB_TRY_ALLOC(dalloc(&c->counters, 16));
     NB_TRY_ALLOC(dalloc(&c->diag, 4));
     NB_TRY_ALLOC(dalloc(&c->err, 1));
-    NB_TRY_ALLOC(dalloc(&c->queue, 1));
+    NB_TRY_ALLOC(dalloc(&c->queue, 2));
+    NB_TRY_ALLOC(dalloc(&c->erow, NB_EROW_SLOTS * 11));
     NB_TRY_ALLOC(dalloc(&c->ewald_part, 8 * 1024));
     NB_TRY_ALLOC(dalloc(&c->ewald_count, 1));
     NB_TRY_ALLOC(dalloc(&c->col_of, N));
@@ -338,6 +340,7 @@ void nb_destroy(nb_ctx *c) {
     dfree(c->diag);
     dfree(c->err);
     dfree(c->queue);
+    dfree(c->erow);
     dfree(c->ewald_part);
     dfree(c->ewald_count);
     for (int k = 0; k < NB_TRACE_KINDS; k++) {

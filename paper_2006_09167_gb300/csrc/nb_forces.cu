@@ -29,7 +29,10 @@ using namespace nbk;
 
 namespace {
 
-constexpr int kFW = 4;  // warps (work items) per block
+// Warps (work items) per block: one.  The kernel's registers (96 a thread) then
+// allow 21 resident warps per SM instead of the 20 of five 4-warp blocks, and no
+// warp waits at a block barrier for the others to run out of work.
+constexpr int kFW = 1;
 constexpr int kLj3MaxT = 8;  // largest type count with the T^3 parameter table (48 B x 512 = 24 KB)
 
 // dynamic shared memory of the force kernel: the T x T tables, and for LJ3 the T^3 ones
@@ -104,11 +107,14 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
         if (lane == 0) claim = atomicAdd(v.queue, 1);
         w = n_warps + __shfl_sync(full, claim, 0);
     }
-    // the block's four rows of partial sums, added in FP64 to the outputs (E_LJ, f E_C,
-    // -1/2 of the virial) by 11 atomics per block of the persistent grid: no separate fold
-    // launch, and the blocks finish at different times, so the atomics hardly contend
+    // the block's rows of partial sums (one per warp), added in FP64 to slot (block mod
+    // NB_EROW_SLOTS) of the context's block sums: the blocks spread their atomics over 32
+    // addresses per value, so that they neither contend nor leave a backlog that would slow
+    // the next kernel.  The last block to finish (a counter, no waiting) adds the slots and
+    // writes the outputs (E_LJ, f E_C, -1/2 of the virial).
     if (EN || VIR) {
         __shared__ double s_row[kFW][11];
+        __shared__ bool s_last;
         if (lane < 11) s_row[wib][lane] = row;
         __syncthreads();
         const int t = threadIdx.x;
@@ -116,10 +122,20 @@ __global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
             double tot = 0.0;
 #pragma unroll
             for (int q = 0; q < kFW; q++) tot += s_row[q][t];
+            atomicAdd(&v.erow[(blockIdx.x % NB_EROW_SLOTS) * 11 + t], tot);
+            __threadfence();
+        }
+        __syncthreads();
+        if (t == 0) s_last = atomicAdd(&v.queue[1], 1) == (int)gridDim.x - 1;
+        __syncthreads();
+        if (s_last && t < 11) {
+            __threadfence();
+            double tot = 0.0;
+            for (int k = 0; k < NB_EROW_SLOTS; k++) tot += __ldcg(&v.erow[k * 11 + t]);
             if (t < 2) {
-                if (v.e) atomicAdd(&v.e[t], t == 0 ? tot : v.coul_f64 * tot);
+                if (v.e) v.e[t] = t == 0 ? tot : v.coul_f64 * tot;
             } else if (v.vir) {
-                atomicAdd(&v.vir[t - 2], -0.5 * tot);
+                v.vir[t - 2] = -0.5 * tot;
             }
         }
     }
@@ -140,13 +156,14 @@ struct L2Prefetch {
 __global__ void k_gather(int nslots, const int *__restrict__ perm, const float *__restrict__ x,
                          const int *__restrict__ img, const float *__restrict__ q_s, double Lx, double Ly,
                          double Lz, float4 *__restrict__ xq, float4 *__restrict__ fs, double *e, double *vir,
-                         int *err, int *queue, L2Prefetch pf) {
+                         int *err, int *queue, double *erow, L2Prefetch pf) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int t = s; t < NB_EROW_SLOTS * 11; t += gridDim.x * blockDim.x) erow[t] = 0.0;
 #pragma unroll
     for (int r = 0; r < 5; r++)
         if (s < pf.lines[r]) asm volatile("prefetch.global.L2 [%0];" ::"l"(pf.p[r] + (size_t)s * 128));
     if (s == 0) {
-        *queue = 0;
+        queue[0] = queue[1] = 0;
         if (e) e[0] = e[1] = 0.0;
         if (vir)
             for (int k = 0; k < 9; k++) vir[k] = 0.0;
@@ -175,13 +192,15 @@ __global__ void k_gather(int nslots, const int *__restrict__ perm, const float *
 // Sorted-layout mode: zero the caller's sorted force array, the energy / virial
 // outputs and the work-item counter, and prefetch the lists into L2 (as the
 // gather does when it also brings in the positions).
-__global__ void k_prep_sorted(int nslots, float4 *__restrict__ f, double *e, double *vir, int *queue, L2Prefetch pf) {
+__global__ void k_prep_sorted(int nslots, float4 *__restrict__ f, double *e, double *vir, int *queue, double *erow,
+                              L2Prefetch pf) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int t = s; t < NB_EROW_SLOTS * 11; t += gridDim.x * blockDim.x) erow[t] = 0.0;
 #pragma unroll
     for (int r = 0; r < 5; r++)
         if (s < pf.lines[r]) asm volatile("prefetch.global.L2 [%0];" ::"l"(pf.p[r] + (size_t)s * 128));
     if (s == 0) {
-        *queue = 0;
+        queue[0] = queue[1] = 0;
         if (e) e[0] = e[1] = 0.0;
         if (vir)
             for (int k = 0; k < 9; k++) vir[k] = 0.0;
@@ -255,7 +274,7 @@ nb_status nb_launch_gather(nb_ctx *c, const float *x, double *e, double *vir, cu
     const long long threads = std::max<long long>(ns, most);
     k_gather<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ns, c->perm, x, c->img, c->q_s, c->box[0], c->box[1],
                                                                 c->box[2], c->xq, c->fs, e, vir, c->err, c->queue,
-                                                                pf);
+                                                                c->erow, pf);
     NB_CUDA_TRY(cudaGetLastError());
     return NB_OK;
 }
@@ -295,7 +314,7 @@ nb_status nb_launch_forces_sorted(nb_ctx *c, unsigned flags, const float4 *xq, f
     {
         NbTraceScope tr(c, NB_TRACE_GATHER, st);
         c->n_launches++;
-        k_prep_sorted<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ns, f, ee, vv, c->queue, pf);
+        k_prep_sorted<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ns, f, ee, vv, c->queue, c->erow, pf);
     }
     SysView v = nb_make_view(c, f, ee, vv);
     if (v.n_items > 0) {  // the force kernel also adds the energies and the virial to e and vir

@@ -28,6 +28,7 @@
 #define NB_SCL 8           // clusters per super-cluster (2x2x2)
 #define NB_SCA 64          // atoms per super-cluster
 #define NB_MAX_EXCL 16     // exclusion partners per atom
+#define NB_EROW_SLOTS 32   // addresses the force kernel's blocks spread their energy / virial sums over
 #define NB_LJ3_MAX_T 8     // types up to which the T^3 parameter tables are kept (48 B x 512)
 #define NB_MAX_COL 8192    // atoms per grid column (bitonic sort in shared memory)
 #define NB_MAX_TYPES 64
@@ -74,7 +75,8 @@ struct SysView {
     float ew_2bsp;   // 2 beta / sqrt(pi)
     float ew_bt, ew_bt_lo;  // beta / ZMAX as a float pair (X(z) is evaluated in t = z / ZMAX)
     float rc6inv, rc12inv;
-    int *queue;  // work-item counter of the persistent force kernel (zeroed by the gather)
+    int *queue;  // [0] work-item counter of the persistent force kernel, [1] its finished blocks (zeroed by the gather)
+    double *erow;  // [NB_EROW_SLOTS * 11] energy / virial sums of the force kernel's blocks, by slot (zeroed by the gather)
     unsigned short *kept;  // first-use prune fused into the force kernel: half masks per outer entry
     float rin2;            // and its squared inner radius
 };
@@ -189,7 +191,8 @@ struct nb_ctx {
     // diagnostics
     long long *diag = nullptr;  // [4]
     int *err = nullptr;
-    int *queue = nullptr;  // work-item counter of the persistent force kernel
+    int *queue = nullptr;  // [2] work-item counter and finished-block counter of the persistent force kernel
+    double *erow = nullptr;  // [NB_EROW_SLOTS * 11] block sums of energies and virial
     double *ewald_part = nullptr;    // [1024*8] per-block rows of the Ewald exclusion / self kernel
     unsigned *ewald_count = nullptr;  // its finished-block counter (zero between calls)
     int n_sm = 0;          // multiprocessors of the context's device

@@ -273,6 +273,7 @@ extern "C" nb_status nb_forces_small_noalloc(const nb_params *p, const float *x_
     a.v.ew_beta = (float)p->beta;
     a.v.ew_shift = p->coulomb == NB_COULOMB_EWALD ? (float)(erfc(p->beta * rc) / rc) : 0.f;
     a.v.queue = nullptr;
+    a.v.erow = nullptr;
     a.v.kept = nullptr;
     a.v.rin2 = 0.f;
     a.v.ew_beta2 = (float)(p->beta * p->beta);

@@ -34,11 +34,11 @@ struct PruneArgs {
 //    i-atom t of every i-cluster) and writes each entry's surviving mask byte;
 //  k_prune_compact: one warp per item of this part copies the entries whose mask
 //    survived, in their original order, into the inner list.
-// Items of at most 64 entries (the usual splits) are one chunk: the warp that
-// prunes an item also compacts it (COMPACT), one launch and no round trip of the
-// masks through memory.
+// Items of at most 128 entries (every split nb_set_split allows) are one chunk: the
+// warp that prunes an item also compacts it (COMPACT), one launch and no round trip
+// of the masks through memory.
 constexpr int kPruneChunk = 16;     // entries per warp for items longer than kPruneWhole
-constexpr int kPruneWhole = 64;     // items up to this many entries: one warp prunes and compacts them
+constexpr int kPruneWhole = 128;    // items up to this many entries (every split): one warp prunes and compacts them
 
 template <bool COMPACT>
 __global__ void __launch_bounds__(kPW * 32) k_prune_masks(PruneArgs a, int chunks_per_item, int chunk) {
