@@ -22,6 +22,9 @@
 // kernels form exp(-z^2) once and take erfc(z) = exp(-z^2) X(z) and the force
 // from it (nb_pair.cuh), V_C = f qi qj (erfc(z)/r - erfc(beta rc)/rc).
 #include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "nb_pair.cuh"
 
@@ -29,10 +32,10 @@ using namespace nbk;
 
 namespace {
 
-// Warps (work items) per block: one.  The kernel's registers (96 a thread) then
-// allow 21 resident warps per SM instead of the 20 of five 4-warp blocks, and no
-// warp waits at a block barrier for the others to run out of work.
-constexpr int kFW = 1;
+// Warps (work items) per block, W: one where that keeps as many warps resident
+// (few types: small tables per block), so that no warp waits at a block barrier
+// for the others to run out of work; four where one-warp blocks would each hold a
+// copy of large type-pair tables and fewer warps would fit an SM.
 constexpr int kLj3MaxT = 8;  // largest type count with the T^3 parameter table (48 B x 512 = 24 KB)
 
 // dynamic shared memory of the force kernel: the T x T tables, and for LJ3 the T^3 ones
@@ -44,8 +47,9 @@ __host__ __device__ inline size_t forces_smem(int T, bool en, bool lj3) {
 // Persistent: a grid sized to the resident capacity of the GPU, each warp taking
 // the next work item (ordered longest first) from a device counter, so the
 // kernel tail is at most one item long (paper Sec. V.F: tails from uneven work).
-template <int COUL, bool EN, bool VIR, bool PRUNE = false, bool LJ3 = false>
-__global__ void __launch_bounds__(kFW * 32) k_forces(SysView v) {
+template <int COUL, bool EN, bool VIR, bool PRUNE = false, bool LJ3 = false, int W = 4>
+__global__ void __launch_bounds__(W * 32) k_forces(SysView v) {
+    constexpr int kFW = W;
     extern __shared__ float4 s_dyn[];
     const int T = v.T, T2 = T * T, T3 = LJ3 ? T2 * T : 0;
     // float4 arrays first: lje [T2] (EN), l3f [T3], l3e [T3] (EN); then float2: lj [T2], l3s [T3] (EN)
@@ -219,29 +223,56 @@ __global__ void k_unsort(int n, const int *__restrict__ inv, const float4 *__res
     }
 }
 
+// Resident blocks per SM of a force kernel variant (remembered per device and
+// shared-memory size: the force call asks on every launch).
+template <int COUL, bool EN, bool VIR, bool PRUNE, bool LJ3, int W>
+int forces_occupancy(size_t smem) {
+    static std::mutex mu;
+    static std::vector<std::pair<size_t, int>> known;  // (smem * 64 + device, blocks)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t key = smem * 64 + (size_t)(dev & 63);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const auto &k : known)
+            if (k.first == key) return k.second;
+    }
+    if (smem > 16 * 1024)
+        cudaFuncSetAttribute(k_forces<COUL, EN, VIR, PRUNE, LJ3, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_forces<COUL, EN, VIR, PRUNE, LJ3, W>, W * 32, smem) !=
+            cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    std::lock_guard<std::mutex> lk(mu);
+    if (known.size() < 64) known.emplace_back(key, occ);
+    return occ;
+}
+
 // Returns the number of warps of the launch.
-template <int COUL, bool EN, bool VIR, bool PRUNE = false, bool LJ3 = false>
+template <int COUL, bool EN, bool VIR, bool PRUNE = false, bool LJ3 = false, int W = 4>
 int launch_forces_t(const SysView &v, int n_sm, cudaStream_t st) {
+    constexpr int kFW = W;
     const size_t smem = forces_smem(v.T, EN, LJ3);
     // the type-pair tables of many types, with the 17 KB of static staging arrays,
     // exceed the default 48 KB of shared memory (64 types: 96 KB of tables); opt in
     // to the larger carve-out, at lower occupancy
-    if (smem > 16 * 1024)
-        cudaFuncSetAttribute(k_forces<COUL, EN, VIR, PRUNE, LJ3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_forces<COUL, EN, VIR, PRUNE, LJ3>, kFW * 32, smem) != cudaSuccess ||
-        occ < 1)
-        occ = 1;
+    const int occ = forces_occupancy<COUL, EN, VIR, PRUNE, LJ3, W>(smem);
     const int blocks = std::min((v.n_items + kFW - 1) / kFW, std::max(n_sm, 1) * occ);
-    k_forces<COUL, EN, VIR, PRUNE, LJ3><<<blocks, kFW * 32, smem, st>>>(v);
+    k_forces<COUL, EN, VIR, PRUNE, LJ3, W><<<blocks, kFW * 32, smem, st>>>(v);
     return blocks * kFW;
 }
 
-// the T^3 parameter table where it fits (few types), the T x T tables otherwise
+// the T^3 parameter table where it fits (few types), the T x T tables otherwise; for
+// the former, one-warp blocks where they keep as many warps resident as 4-warp ones
 template <int COUL, bool EN, bool VIR>
 int launch_pick(const SysView &v, int n_sm, cudaStream_t st) {
-    return v.T <= kLj3MaxT ? launch_forces_t<COUL, EN, VIR, false, true>(v, n_sm, st)
-                           : launch_forces_t<COUL, EN, VIR, false, false>(v, n_sm, st);
+    if (v.T > kLj3MaxT) return launch_forces_t<COUL, EN, VIR, false, false, 4>(v, n_sm, st);
+    const size_t smem = forces_smem(v.T, EN, true);
+    const int warps1 = forces_occupancy<COUL, EN, VIR, false, true, 1>(smem);
+    const int warps4 = 4 * forces_occupancy<COUL, EN, VIR, false, true, 4>(smem);
+    return warps1 >= warps4 ? launch_forces_t<COUL, EN, VIR, false, true, 1>(v, n_sm, st)
+                            : launch_forces_t<COUL, EN, VIR, false, true, 4>(v, n_sm, st);
 }
 
 }  // namespace
