@@ -60,12 +60,13 @@ __device__ __forceinline__ float ew_h(float s) {
 // exp(-x) for 0 <= x < 80: x = n ln2 + u (Cody-Waite reduction; n * LN2_HI is
 // exact), exp(-u) by the degree-7 polynomial 1 + w q(w) with w = -u, times 2^-n
 //
-// n = rint(x log2 e) by the 1.5 * 2^23 shift: m = x log2 e + 1.5 * 2^23 rounds to an
-// integer whose low mantissa bits hold n (0 <= n < 2^22), -n = 1.5 * 2^23 - m is exact,
-// and the scale 2^-n has the bits 0x3f800000 - (bits(m) << 23).  Same n as rintf
-// (round half to even) without the float -> int conversions.
+// n = rint(x log2 e) by the 1.5 * 2^23 shift in one FMA: m = x log2 e + 1.5 * 2^23,
+// rounded once, is an integer whose low mantissa bits hold n (0 <= n < 2^22; ties go
+// to even, so n is the round-half-even integer nearest the exact product), -n =
+// 1.5 * 2^23 - m is exact, and the scale 2^-n has the bits 0x3f800000 - (bits(m) << 23).
+// No float -> int conversions.
 __device__ __forceinline__ float ew_expm(float x) {
-    const float m = __fadd_rn(__fmul_rn(x, NB_EXP_LOG2E), 12582912.0f);
+    const float m = __fmaf_rn(x, NB_EXP_LOG2E, 12582912.0f);
     const float nn = __fsub_rn(12582912.0f, m);
     float u = fmaf(nn, NB_EXP_LN2_HI, x);
     u = fmaf(nn, NB_EXP_LN2_LO, u);
@@ -135,8 +136,7 @@ __device__ __forceinline__ float2 ew_h2(float2 s) {
 }
 
 __device__ __forceinline__ float2 ew_expm2(float2 x) {
-    const float2 nl = pmul(x, p2(NB_EXP_LOG2E));
-    const float2 m = padd(nl, p2(12582912.0f));
+    const float2 m = pfma(x, p2(NB_EXP_LOG2E), p2(12582912.0f));
     const float2 nn = psub(p2(12582912.0f), m);  // -n, exact
     float2 u = pfma(nn, p2(NB_EXP_LN2_HI), x);
     u = pfma(nn, p2(NB_EXP_LN2_LO), u);
@@ -474,14 +474,27 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             }
             const Lj2 lj = LJ3 ? lj_triple<EN>(ljt, tio * v.T + tjj) : lj_gather<EN>(ljt, tio + tj0, tio + tj1);
             const float2 p = pair_phi2<COUL, EN>(v, lj, dx, dy, dz, qi2, jq, b0, b1, elj2, ec2);
-            const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
+            // force p d on i and -p d on j
             float *fk = s_fi + k * 96 + lane;
-            fk[0] += ax.x + ax.y;
-            fk[32] += ay.x + ay.y;
-            fk[64] += az.x + az.y;
-            fjx = psub(fjx, ax);
-            fjy = psub(fjy, ay);
-            fjz = psub(fjz, az);
+            // each product fused into its accumulation where that measured faster (the T^3-table
+            // kernels, except forces + virial without energies; the others were 3-4% slower)
+            if (LJ3 && (EN || !VIR)) {
+                fk[0] = __fmaf_rn(p.y, dx.y, __fmaf_rn(p.x, dx.x, fk[0]));
+                fk[32] = __fmaf_rn(p.y, dy.y, __fmaf_rn(p.x, dy.x, fk[32]));
+                fk[64] = __fmaf_rn(p.y, dz.y, __fmaf_rn(p.x, dz.x, fk[64]));
+                const float2 pn = pneg(p);
+                fjx = pfma(pn, dx, fjx);
+                fjy = pfma(pn, dy, fjy);
+                fjz = pfma(pn, dz, fjz);
+            } else {
+                const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
+                fk[0] += ax.x + ax.y;
+                fk[32] += ay.x + ay.y;
+                fk[64] += az.x + az.y;
+                fjx = psub(fjx, ax);
+                fjy = psub(fjy, ay);
+                fjz = psub(fjz, az);
+            }
         }
         // i-clusters that the prune kept for one j-half only: two such i-clusters share a
         // packed iteration (each component its own i-atom, j-atom and mask bit)
@@ -503,32 +516,31 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
                                          s_ti[kb * NB_CL + ti] + (ub ? tj1 : tj0));
             const float2 p = pair_phi2<COUL, EN>(v, lj, dx, dy, dz, make_float2(xia.w, xib.w),
                                                  make_float2(xja.w, xjb.w), ba, bb, elj2, ec2);
-            const float2 ax = pmul(p, dx), ay = pmul(p, dy), az = pmul(p, dz);
             float *fa = s_fi + ka * 96 + lane;
             float *fb = s_fi + kb * 96 + lane;
-            fa[0] += ax.x;
-            fa[32] += ay.x;
-            fa[64] += az.x;
-            fb[0] += ax.y;
-            fb[32] += ay.y;
-            fb[64] += az.y;
+            fa[0] = __fmaf_rn(p.x, dx.x, fa[0]);
+            fa[32] = __fmaf_rn(p.x, dy.x, fa[32]);
+            fa[64] = __fmaf_rn(p.x, dz.x, fa[64]);
+            fb[0] = __fmaf_rn(p.y, dx.y, fb[0]);
+            fb[32] = __fmaf_rn(p.y, dy.y, fb[32]);
+            fb[64] = __fmaf_rn(p.y, dz.y, fb[64]);
             if (ua) {
-                fjx.y -= ax.x;
-                fjy.y -= ay.x;
-                fjz.y -= az.x;
+                fjx.y = __fmaf_rn(-p.x, dx.x, fjx.y);
+                fjy.y = __fmaf_rn(-p.x, dy.x, fjy.y);
+                fjz.y = __fmaf_rn(-p.x, dz.x, fjz.y);
             } else {
-                fjx.x -= ax.x;
-                fjy.x -= ay.x;
-                fjz.x -= az.x;
+                fjx.x = __fmaf_rn(-p.x, dx.x, fjx.x);
+                fjy.x = __fmaf_rn(-p.x, dy.x, fjy.x);
+                fjz.x = __fmaf_rn(-p.x, dz.x, fjz.x);
             }
             if (ub) {
-                fjx.y -= ax.y;
-                fjy.y -= ay.y;
-                fjz.y -= az.y;
+                fjx.y = __fmaf_rn(-p.y, dx.y, fjx.y);
+                fjy.y = __fmaf_rn(-p.y, dy.y, fjy.y);
+                fjz.y = __fmaf_rn(-p.y, dz.y, fjz.y);
             } else {
-                fjx.x -= ax.y;
-                fjy.x -= ay.y;
-                fjz.x -= az.y;
+                fjx.x = __fmaf_rn(-p.y, dx.y, fjx.x);
+                fjy.x = __fmaf_rn(-p.y, dy.y, fjy.x);
+                fjz.x = __fmaf_rn(-p.y, dz.y, fjz.x);
             }
         }
         if (one) {  // the last single-half i-cluster: one pair per lane
@@ -541,19 +553,18 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
             const float p = pair_phi<COUL, EN>(v, ljt.lj, ljt.lje, d, xi.w, xj.w, tio + (upper ? tj1 : tj0), b, elj_e,
                                                ec_e);
-            const float ax = p * d.x, ay = p * d.y, az = p * d.z;
             float *fk = s_fi + k * 96 + lane;
-            fk[0] += ax;
-            fk[32] += ay;
-            fk[64] += az;
+            fk[0] = __fmaf_rn(p, d.x, fk[0]);
+            fk[32] = __fmaf_rn(p, d.y, fk[32]);
+            fk[64] = __fmaf_rn(p, d.z, fk[64]);
             if (upper) {
-                fjx.y -= ax;
-                fjy.y -= ay;
-                fjz.y -= az;
+                fjx.y = __fmaf_rn(-p, d.x, fjx.y);
+                fjy.y = __fmaf_rn(-p, d.y, fjy.y);
+                fjz.y = __fmaf_rn(-p, d.z, fjz.y);
             } else {
-                fjx.x -= ax;
-                fjy.x -= ay;
-                fjz.x -= az;
+                fjx.x = __fmaf_rn(-p, d.x, fjx.x);
+                fjy.x = __fmaf_rn(-p, d.y, fjy.x);
+                fjz.x = __fmaf_rn(-p, d.z, fjz.x);
             }
         }
         if (EN) {

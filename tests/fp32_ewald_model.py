@@ -61,7 +61,8 @@ def _split(v):
 def expm32(x):
     """exp(-x) as the kernels evaluate it, in FP32."""
     c = constants()
-    n = np.rint((x * c["NB_EXP_LOG2E"]).astype(f32)).astype(f32)
+    # n = rint of the exact product x log2e (the kernels round x log2e + 1.5 * 2^23 once, in an FMA)
+    n = np.rint(np.asarray(x, np.float64) * np.float64(c["NB_EXP_LOG2E"])).astype(f32)
     u = _fma(-n, c["NB_EXP_LN2_HI"], x)
     u = _fma(-n, c["NB_EXP_LN2_LO"], u)
     w = (-u).astype(f32)

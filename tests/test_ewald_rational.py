@@ -38,7 +38,8 @@ def horner(coefs, t):
 
 
 def expm(c, x):
-    n = np.rint((x * c["NB_EXP_LOG2E"]).astype(f32)).astype(f32)
+    # n = rint of the exact product x log2e (the kernels round x log2e + 1.5 * 2^23 once, in an FMA)
+    n = np.rint(np.asarray(x, np.float64) * np.float64(c["NB_EXP_LOG2E"])).astype(f32)
     u = fma(-n, c["NB_EXP_LN2_HI"], x)
     u = fma(-n, c["NB_EXP_LN2_LO"], u)
     w = (-u).astype(f32)
