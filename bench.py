@@ -62,12 +62,12 @@ FLOPS_PER_PAIR_ROOFLINE = {"ewald": 53, "rf": 41, "none": 33}
 # DRAM bytes (read + write) of one k_forces<Ewald, energy, virial> launch on the
 # 96k box, from the committed ncu summary of that kernel (the capture named in
 # FORCE_KERNEL_CAPTURE); None whenever the force kernel has changed since it was taken.
-FORCE_KERNEL_DRAM_BYTES = 7_698_688
+FORCE_KERNEL_DRAM_BYTES = 7_698_176
 # From the same capture: FP32 (FMA) pipe and issue-slot utilisation of that launch,
 # in percent of active cycles (what bounds the kernel; None with the bytes above).
-FORCE_KERNEL_NCU_PCT = {"fma_pipe": 60.7, "issue_slots": 70.1}
+FORCE_KERNEL_NCU_PCT = {"fma_pipe": 58.9, "issue_slots": 69.3}
 FORCE_KERNEL_CAPTURE = ("profiles/k_forces_spce_water_96k.md, mid-life launch of "
-                        "'bench.py --profile --profile-case step --split 24', one-warp blocks (cold L2, one launch)")
+                        "'bench.py --profile --profile-case step --split 24', fused force updates (cold L2, one launch)")
 
 
 def rank_env():
