@@ -474,11 +474,11 @@ __device__ __forceinline__ void process_item(const SysView &v, int w, int nj, co
             }
             const Lj2 lj = LJ3 ? lj_triple<EN>(ljt, tio * v.T + tjj) : lj_gather<EN>(ljt, tio + tj0, tio + tj1);
             const float2 p = pair_phi2<COUL, EN>(v, lj, dx, dy, dz, qi2, jq, b0, b1, elj2, ec2);
-            // force p d on i and -p d on j
+            // force p d on i and -p d on j.  Each product is fused into its accumulation where
+            // that measured faster: the T^3-table kernels for forces alone and for forces +
+            // energies + virial.  With energies or the virial alone, and in the T x T-table
+            // kernels, the fused form was 3-5% slower.
             float *fk = s_fi + k * 96 + lane;
-            // each product fused into its accumulation where that measured faster: the T^3-table
-            // kernels for forces alone and for forces + energies + virial (with energies or the
-            // virial alone, and in the T x T-table kernels, the fused form was 3-5% slower)
             if (LJ3 && EN == VIR) {
                 fk[0] = __fmaf_rn(p.y, dx.y, __fmaf_rn(p.x, dx.x, fk[0]));
                 fk[32] = __fmaf_rn(p.y, dy.y, __fmaf_rn(p.x, dy.x, fk[32]));
